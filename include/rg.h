@@ -1,0 +1,207 @@
+/*
+ * rg.h -- C ABI of the GB300 rank-Greville recursive least-squares library (librg.so).
+ *
+ * The method (Staub & Steinmann, "Efficient Recursive Least Squares Solver for
+ * Rank-Deficient Matrices", arXiv 2106.11594) keeps a full-rank factorization
+ * A_n = B_n C_n of the n x m observation matrix (Section 2.1, Eq. label_eq_mat_prod):
+ * C_n (r x m) holds r linearly independent observed rows, Ct_n = (C_n C_n^T)^-1 C_n is
+ * its dual basis, and P_n^-1 = (B_n^T B_n)^-1 is r x r. For every new observation
+ * (Gamma, y) it projects Gamma onto span(C_n) (gamma = Ct_n Gamma), forms the rejection
+ * Gamma_r = Gamma - C_n^T gamma, runs the rank test of Eq. label_eq_eps, then either
+ * appends a basis row (Theorem 6, independent case) or applies the rank-preserving
+ * Sherman-Morrison update of P^-1 (Theorem 6, dependent case), and refreshes the
+ * minimum-norm least-squares solution X = A^+ Y (Theorems 4 and 5; Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ *  - Every matrix is row-major. A block of k observations is a k x m array whose row i
+ *    is Gamma_i^T; targets are a length-k array.
+ *  - Pointers documented as "device" must be CUDA device (or managed) memory on the
+ *    device that was current when the state was created; "host" pointers are ordinary
+ *    CPU memory. The caller owns every buffer it passes; the library owns the state.
+ *  - Calls are asynchronous on the state's CUDA stream unless documented as
+ *    synchronising. Arguments are validated on the host before anything is enqueued:
+ *    a bad argument returns RG_EINVAL and enqueues nothing.
+ *  - Errors found on the device (non-finite rows, rank capacity exceeded, a bounded
+ *    wait that ran out) are recorded in a device status word and returned by the next
+ *    synchronising call (rg_solution, rg_rank, rg_sync). The row that raised the error
+ *    and every later row of the same call are not applied; the state stays as it was
+ *    after the last applied row; rg_rows_seen reports how many rows were applied.
+ *  - rg_last_error() returns a thread-local message describing the last failure.
+ *  - Nothing here falls back to the CPU: without a usable CUDA device every call that
+ *    needs one returns RG_ECUDA.
+ */
+#ifndef RG_H
+#define RG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rg_state rg_state; /* one recursive least-squares stream (opaque)   */
+typedef struct rg_batch rg_batch; /* many independent streams of uneven shape       */
+
+typedef enum {
+  RG_OK = 0,
+  RG_EINVAL = 1,      /* invalid argument (checked on the host, nothing enqueued)   */
+  RG_ENOMEM = 2,      /* device or host allocation failed                           */
+  RG_ECUDA = 3,       /* a CUDA runtime call failed (message in rg_last_error)       */
+  RG_ECAPACITY = 4,   /* an independent row arrived while rank == r_max              */
+  RG_ENONFINITE = 5,  /* a row or target contained NaN or Inf                        */
+  RG_ETIMEOUT = 6     /* a bounded device-side wait gave up (state must be reset)     */
+} rg_status;
+
+/* Flags of rg_init / rg_batch_init (OR them together). */
+enum {
+  RG_FP64 = 0,        /* all arithmetic in FP64                                      */
+  RG_MIXED = 1,       /* projections in FP32; rank test, denominators, P^-1 and w in
+                         FP64; candidate rows are re-decided in FP64 (see rg_init)   */
+  RG_TEST_REL = 0,    /* independent iff ||Gamma_r|| > eps ||Gamma||                  */
+  RG_TEST_PAPER = 2   /* dependent iff ||Gamma_r|| < eps or ||Gamma_r|| < eps ||Gamma||
+                         (Eq. label_eq_eps, both clauses)                            */
+};
+
+/*
+ * rg_init -- create an empty stream (rank 0, X = 0) for observations of length m.
+ *   out        host; receives the new state.
+ *   m          number of regressors (columns), >= 1.
+ *   tol        rank-test threshold eps of Eq. label_eq_eps. tol <= 0 selects the
+ *              paper's default (m^2 r + m r + m) eps_M, r the rank before the row.
+ *              Must not be NaN.
+ *   flags      RG_FP64 or RG_MIXED, OR-ed with RG_TEST_REL or RG_TEST_PAPER.
+ *              In RG_MIXED mode a row whose FP32 relative rejection
+ *              ||Gamma_r|| / ||Gamma|| exceeds 1e-5 is recomputed and decided in FP64;
+ *              rows below that floor are taken as dependent.
+ *   r_max      capacity of the basis (maximum rank), 1..m; <= 0 means m.
+ *   cuda_stream  cudaStream_t on which all work of this state is enqueued (NULL: the
+ *              legacy default stream). Device memory is allocated here, once.
+ * Returns RG_OK, RG_EINVAL, RG_ENOMEM or RG_ECUDA.
+ */
+rg_status rg_init(rg_state** out, int64_t m, double tol, int flags, int64_t r_max,
+                  void* cuda_stream);
+
+/*
+ * rg_add_rows -- apply Algorithm 1 to k new observations, in order.
+ *   Gamma      device, k x m row-major FP64 (row i = Gamma_i^T).
+ *   y          device, k FP64 targets.
+ *   k          number of rows, >= 0 (0 is a no-op).
+ *   indep_out  device, k bytes, may be NULL: indep_out[i] = 1 if row i grew the rank,
+ *              0 if it was dependent (rows not applied because of an error keep 0xFF).
+ * The result equals k sequential single-row updates in exact arithmetic (the rows are
+ * projected as one block and the rank changes inside the block are applied in order).
+ * Asynchronous; device errors surface at the next synchronising call.
+ */
+rg_status rg_add_rows(rg_state* st, const double* Gamma, const double* y, int64_t k,
+                      uint8_t* indep_out);
+
+/*
+ * rg_add_rows_host -- same as rg_add_rows for HOST buffers: the rows are copied to the
+ * device inside the call (in chunks through library-owned staging memory) and the call
+ * returns once the host buffers may be reused. indep_out is host memory (may be NULL).
+ */
+rg_status rg_add_rows_host(rg_state* st, const double* Gamma, const double* y, int64_t k,
+                           uint8_t* indep_out);
+
+/*
+ * rg_solution -- materialise X = A^+ Y (length m) into device memory X.
+ *   rank_out   host, may be NULL: receives the current rank (this synchronises).
+ * Synchronising when rank_out != NULL; returns any pending device error.
+ */
+rg_status rg_solution(rg_state* st, double* X, int64_t* rank_out);
+
+/* rg_solution_host -- rg_solution into HOST memory X (m doubles). Synchronising. */
+rg_status rg_solution_host(rg_state* st, double* X, int64_t* rank_out);
+
+/* rg_rank -- current rank r into *rank_out (host). Synchronising. */
+rg_status rg_rank(rg_state* st, int64_t* rank_out);
+
+/* rg_rows_seen -- number of rows applied since init/reset into *rows_out (host).
+ * Synchronising. */
+rg_status rg_rows_seen(rg_state* st, int64_t* rows_out);
+
+/* rg_sync -- wait for the state's stream and return any pending device error
+ * (the error is cleared once returned). */
+rg_status rg_sync(rg_state* st);
+
+/* rg_reset -- return to the empty state (rank 0, X = 0) without reallocating.
+ * Asynchronous. */
+rg_status rg_reset(rg_state* st);
+
+/*
+ * rg_export -- copy the factorization for inspection. Device pointers, each may be NULL:
+ *   C (r x m), Ct (r x m), Pinv (r x r), w (r; X = Ct^T w), basis_rows (r int64: the
+ *   0-based index, counted from init/reset, of the input row stored in each row of C).
+ *   capacity   number of rows each of C/Ct/w/basis_rows can hold (>= current rank,
+ *              else RG_EINVAL); Pinv must hold capacity x capacity and is written with
+ *              row stride r.
+ *   rank_out   host, receives r. Synchronising.
+ */
+rg_status rg_export(rg_state* st, double* C, double* Ct, double* Pinv, double* w,
+                    int64_t* basis_rows, int64_t capacity, int64_t* rank_out);
+
+/* rg_set_stream -- enqueue later work of this state on another cudaStream_t. */
+rg_status rg_set_stream(rg_state* st, void* cuda_stream);
+
+/* rg_free -- release the state (synchronises its stream first). NULL is a no-op. */
+rg_status rg_free(rg_state* st);
+
+/* ------------------------------------------------------------------------------------
+ * Batched form: B independent streams of uneven (n_b, m_b) in one persistent kernel.
+ * Packed layout: instance b's rows are Gamma_packed[elem_offsets[b] .. elem_offsets[b+1])
+ * viewed as n_b x m_b row-major, with n_b = row_offsets[b+1] - row_offsets[b];
+ * its targets are y_packed[row_offsets[b] .. row_offsets[b+1]).
+ * ------------------------------------------------------------------------------------ */
+
+/*
+ * rg_batch_init -- create B empty streams.
+ *   m       host, B column counts (each >= 1).
+ *   r_max   host, B capacities (NULL: r_max[b] = m[b]).
+ *   tol, flags, cuda_stream: as rg_init (shared by all instances).
+ */
+rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol, int flags,
+                        const int64_t* r_max, void* cuda_stream);
+
+/*
+ * rg_batch_add_rows -- append a block of rows to every instance (n_b may be 0).
+ *   Gamma_packed, y_packed  device FP64, packed as above.
+ *   row_offsets, elem_offsets  device int64, B+1 entries each; elem_offsets[b+1] -
+ *              elem_offsets[b] must equal n_b m_b (checked on the device: a mismatch
+ *              sets RG_EINVAL in the status word and skips the instance).
+ *   indep_out  device, sum(n_b) bytes in row order, may be NULL.
+ * Instances are scheduled longest-first (by n_b m_b r_max_b) over persistent CTAs.
+ */
+rg_status rg_batch_add_rows(rg_batch* bt, const double* Gamma_packed,
+                            const int64_t* row_offsets, const int64_t* elem_offsets,
+                            const double* y_packed, uint8_t* indep_out);
+
+/*
+ * rg_batch_solution -- X_packed[x_offsets[b] .. + m_b) = X of instance b.
+ *   X_packed   device FP64.
+ *   x_offsets  device int64, B+1 entries (NULL: packed back to back by m_b).
+ *   ranks_out  device int64, B entries, may be NULL.
+ * Asynchronous.
+ */
+rg_status rg_batch_solution(rg_batch* bt, double* X_packed, const int64_t* x_offsets,
+                            int64_t* ranks_out);
+
+/* rg_batch_sync -- wait and return any pending device error of the batch. */
+rg_status rg_batch_sync(rg_batch* bt);
+
+/* rg_batch_reset -- every instance back to the empty state. Asynchronous. */
+rg_status rg_batch_reset(rg_batch* bt);
+
+/* rg_batch_free -- release (synchronises first). NULL is a no-op. */
+rg_status rg_batch_free(rg_batch* bt);
+
+/* Thread-local description of the last error returned on this thread ("" if none). */
+const char* rg_last_error(void);
+
+/* Library version string. */
+const char* rg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RG_H */

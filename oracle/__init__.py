@@ -1,0 +1,9 @@
+"""CPU oracle for the rank-Greville recursive least-squares update (TEST INFRASTRUCTURE).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package. It shares no code with the CUDA library and never imports it.
+
+  * ``oracle.fp64``   -- ctypes wrapper of ``rg_oracle.c`` (plain FP64 Algorithm 1).
+  * ``oracle.exact``  -- exact-rational Algorithm 1 and the Theorem 1 route (fractions).
+  * ``oracle.checks`` -- Penrose conditions, invariants and the Section 4.2 metrics.
+"""

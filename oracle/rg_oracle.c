@@ -1,0 +1,273 @@
+/*
+ * rg_oracle.c -- plain, slow, single-threaded FP64 rank-Greville (TEST INFRASTRUCTURE).
+ *
+ * This file is the CPU oracle that the CUDA path is checked against. Only the tests,
+ * the smoke check and the benchmark's CPU-baseline leg load it. It shares no code,
+ * header or constant with the CUDA library.
+ *
+ * What it computes: Algorithm 1 ("UpdateLeastSquares", Section 3), one row at a time,
+ * in the paper's order and notation, with plain left-to-right loops and no BLAS:
+ *
+ *   gamma   = Ct Gamma                              (Eq. label_eq_gnplusoneproj)
+ *   Gamma_r = Gamma - C^T gamma                     (rejection, Section 2.1)
+ *   if Gamma_r != 0 (threshold test, Eq. label_eq_eps):
+ *       K   = Gamma_r / ||Gamma_r||^2               (Theorem 4)
+ *       C   = [C ; Gamma^T]                         (Eq. label_eq_Cnplusone_indep_update)
+ *       Ct  = [Ct - gamma K^T ; K^T]                (Eq. label_eq_Cnplusonetilde_indep_update)
+ *       P^-1 = diag(P^-1, 1)                        (Eq. label_eq_Pnplusoneinv_indep_update)
+ *   else:
+ *       zeta = P^-1 gamma                           (Eq. label_eq_znplusone)
+ *       K    = Ct^T zeta / (1 + gamma^T zeta)       (Theorem 5)
+ *       P^-1 = P^-1 - zeta zeta^T / (1 + gamma^T zeta)  (Eq. label_eq_Pnplusoneinv_lindep_update)
+ *   X = X + K (y - Gamma^T X)                       (Eq. label_eq_recursive_least_squares)
+ *
+ * Readings of the paper taken here (each listed in the design notes):
+ *  - Threshold (Eq. label_eq_eps). Two modes. REL (default): independent iff
+ *    ||Gamma_r|| > eps ||Gamma||. PAPER: dependent iff ||Gamma_r|| < eps or
+ *    ||Gamma_r|| < eps ||Gamma||. Both are evaluated in squared form in FP64
+ *    (s = ||Gamma_r||^2, t = ||Gamma||^2; monotone, so equivalent up to rounding).
+ *  - eps = tol when tol > 0, else the paper's default (m^2 r + m r + m) eps_M with r the
+ *    rank before the row and eps_M = 2^-52 (Section 4.2 states eps_M = 2.22e-16).
+ *  - P^-1 is updated as a full matrix exactly as printed, with no symmetrisation.
+ *  - A row that would make the rank exceed r_max stops the stream with status 4
+ *    (capacity) and leaves the state as it was before that row.
+ *
+ * The `mutation` argument of rgo_solve_mut plants one deliberate mistake (a dropped
+ * term, a wrong sign, a wrong index or a transposed operand) so that the tests can show
+ * that the oracle's pins catch it. rgo_solve always runs with mutation 0.
+ */
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define RGO_TEST_REL 0
+#define RGO_TEST_PAPER 2
+
+typedef struct {
+  int64_t m, r_max, r;
+  double tol;
+  int test_mode;
+  int mutation;
+  double *C;    /* r_max x m, row i = i-th basis row (a selected input row)      */
+  double *Ct;   /* r_max x m, row i = i-th dual basis row                          */
+  double *Pinv; /* r_max x r_max, leading r x r block is P^-1 = (B^T B)^-1         */
+  double *X;    /* m, current minimum-norm least-squares solution                  */
+  double *gamma, *Gr, *zeta, *K;
+  int64_t *basis_rows;
+  int64_t rows_seen;
+} rgo_state;
+
+static int rgo_alloc(rgo_state *st, int64_t m, int64_t r_max, double tol, int test_mode) {
+  memset(st, 0, sizeof(*st));
+  st->m = m;
+  st->r_max = r_max;
+  st->tol = tol;
+  st->test_mode = test_mode;
+  st->C = (double *)calloc((size_t)(r_max * m), sizeof(double));
+  st->Ct = (double *)calloc((size_t)(r_max * m), sizeof(double));
+  st->Pinv = (double *)calloc((size_t)(r_max * r_max + 1), sizeof(double));
+  st->X = (double *)calloc((size_t)m, sizeof(double));
+  st->gamma = (double *)calloc((size_t)(r_max + 1), sizeof(double));
+  st->zeta = (double *)calloc((size_t)(r_max + 1), sizeof(double));
+  st->Gr = (double *)calloc((size_t)m, sizeof(double));
+  st->K = (double *)calloc((size_t)m, sizeof(double));
+  st->basis_rows = (int64_t *)calloc((size_t)(r_max + 1), sizeof(int64_t));
+  if (!st->C || !st->Ct || !st->Pinv || !st->X || !st->gamma || !st->zeta || !st->Gr ||
+      !st->K || !st->basis_rows)
+    return 2;
+  return 0;
+}
+
+static void rgo_release(rgo_state *st) {
+  free(st->C); free(st->Ct); free(st->Pinv); free(st->X); free(st->gamma);
+  free(st->zeta); free(st->Gr); free(st->K); free(st->basis_rows);
+  memset(st, 0, sizeof(*st));
+}
+
+#define CM(i, c) st->C[(i) * st->m + (c)]
+#define CT(i, c) st->Ct[(i) * st->m + (c)]
+#define PI(i, j) st->Pinv[(i) * st->r_max + (j)]
+
+/* Threshold of Eq. label_eq_eps in squared form: returns 1 iff the row is independent. */
+static int rgo_is_independent(const rgo_state *st, double s, double t) {
+  double eps = st->tol;
+  if (!(eps > 0.0)) {
+    double m = (double)st->m, r = (double)st->r;
+    eps = (m * m * r + m * r + m) * DBL_EPSILON;
+  }
+  double e2 = eps * eps;
+  if (st->test_mode == RGO_TEST_PAPER) return !(s < e2 || s < e2 * t);
+  return s > e2 * t;
+}
+
+/* One call of UpdateLeastSquares(Gamma, y, X, C, Ct, P^-1). Returns 1 if the row was
+ * independent, 0 if dependent, -4 on capacity overflow (state untouched). */
+static int rgo_update(rgo_state *st, const double *G, double y) {
+  const int64_t m = st->m, r = st->r;
+  const int mut = st->mutation;
+  /* gamma <- Ct Gamma */
+  for (int64_t i = 0; i < r; ++i) {
+    double acc = 0.0;
+    for (int64_t c = 0; c < m; ++c) acc += (mut == 5 ? CM(i, c) : CT(i, c)) * G[c];
+    st->gamma[i] = acc;
+  }
+  /* Gamma_r <- Gamma - C^T gamma */
+  for (int64_t c = 0; c < m; ++c) {
+    double acc = 0.0;
+    for (int64_t i = 0; i < r; ++i) acc += CM(i, c) * st->gamma[i];
+    st->Gr[c] = (mut == 1 ? G[c] + acc : G[c] - acc);
+  }
+  double s = 0.0, t = 0.0;
+  for (int64_t c = 0; c < m; ++c) {
+    s += st->Gr[c] * st->Gr[c];
+    t += G[c] * G[c];
+  }
+  int indep = rgo_is_independent(st, s, t);
+  if (indep) {
+    if (r >= st->r_max) return -4;
+    /* K <- Gamma_r / ||Gamma_r||^2 */
+    for (int64_t c = 0; c < m; ++c) st->K[c] = st->Gr[c] / s;
+    /* Ct <- [Ct - gamma K^T ; K^T] */
+    for (int64_t i = 0; i < r; ++i)
+      for (int64_t c = 0; c < m; ++c)
+        CT(i, c) -= (mut == 2 ? 0.0 : st->gamma[i] * st->K[c]);
+    for (int64_t c = 0; c < m; ++c) CT(r, c) = st->K[c];
+    /* C <- [C ; Gamma^T] */
+    for (int64_t c = 0; c < m; ++c) CM(r, c) = G[c];
+    /* P^-1 <- diag(P^-1, 1) */
+    for (int64_t i = 0; i < r; ++i) {
+      PI(i, r) = 0.0;
+      PI(r, i) = 0.0;
+    }
+    PI(r, r) = 1.0;
+    st->basis_rows[r] = st->rows_seen;
+    st->r = r + 1;
+  } else {
+    /* zeta <- P^-1 gamma */
+    for (int64_t i = 0; i < r; ++i) {
+      double acc = 0.0;
+      for (int64_t j = 0; j < r; ++j) acc += PI(i, j) * st->gamma[mut == 6 ? (j + 1) % r : j];
+      st->zeta[i] = acc;
+    }
+    double gz = 0.0;
+    for (int64_t i = 0; i < r; ++i) gz += st->gamma[i] * st->zeta[i];
+    double d = (mut == 3 ? gz : 1.0 + gz);
+    /* K <- Ct^T zeta / (1 + gamma^T zeta) */
+    for (int64_t c = 0; c < m; ++c) {
+      double acc = 0.0;
+      for (int64_t i = 0; i < r; ++i) acc += CT(i, c) * st->zeta[i];
+      st->K[c] = acc / d;
+    }
+    /* P^-1 <- P^-1 - zeta zeta^T / (1 + gamma^T zeta) */
+    for (int64_t i = 0; i < r; ++i)
+      for (int64_t j = 0; j < r; ++j)
+        PI(i, j) -= (mut == 4 ? 0.0 : st->zeta[i] * st->zeta[j] / d);
+  }
+  /* X <- X + K (y - Gamma^T X) */
+  double gx = 0.0;
+  for (int64_t c = 0; c < m; ++c) gx += G[c] * st->X[c];
+  double dy = (mut == 7 ? y + gx : y - gx);
+  for (int64_t c = 0; c < m; ++c) st->X[c] += st->K[c] * dy;
+  st->rows_seen += 1;
+  return indep;
+}
+
+/*
+ * Solve one stream from scratch (Corollary label_th_full_lstsq): feed the n rows of
+ * A (n x m, row-major) with targets Y in order.
+ *
+ * Outputs (any may be NULL): X (m), rank_out (1), basis_rows (r_max; the input row
+ * index of each basis row), indep (n bytes, 1 = row grew the rank), Ct_out (r_max x m),
+ * Pinv_out (r_max x r_max), C_out (r_max x m), rows_done (1).
+ * Returns 0, 1 (bad arguments), 2 (out of memory) or 4 (rank would exceed r_max; rows
+ * before the offending row are applied, rows_done says how many).
+ */
+int rgo_solve_mut(int64_t n, int64_t m, const double *A, const double *Y, double tol,
+                  int test_mode, int64_t r_max, int mutation, double *X, int64_t *rank_out,
+                  int64_t *basis_rows, uint8_t *indep, double *Ct_out, double *Pinv_out,
+                  double *C_out, int64_t *rows_done) {
+  if (n < 0 || m <= 0 || (n > 0 && (!A || !Y)) || tol != tol) return 1;
+  if (r_max <= 0) r_max = m;
+  if (r_max > m) r_max = m;
+  rgo_state st;
+  if (rgo_alloc(&st, m, r_max, tol, test_mode)) {
+    rgo_release(&st);
+    return 2;
+  }
+  st.mutation = mutation;
+  int status = 0;
+  int64_t i = 0;
+  for (; i < n; ++i) {
+    int res = rgo_update(&st, A + i * m, Y[i]);
+    if (res == -4) {
+      status = 4;
+      break;
+    }
+    if (indep) indep[i] = (uint8_t)res;
+  }
+  if (rows_done) *rows_done = i;
+  if (X) memcpy(X, st.X, (size_t)m * sizeof(double));
+  if (rank_out) *rank_out = st.r;
+  if (basis_rows) memcpy(basis_rows, st.basis_rows, (size_t)st.r * sizeof(int64_t));
+  if (Ct_out) memcpy(Ct_out, st.Ct, (size_t)(st.r * m) * sizeof(double));
+  if (C_out) memcpy(C_out, st.C, (size_t)(st.r * m) * sizeof(double));
+  if (Pinv_out) {
+    for (int64_t a = 0; a < st.r; ++a)
+      for (int64_t b = 0; b < st.r; ++b) Pinv_out[a * st.r + b] = st.Pinv[a * st.r_max + b];
+  }
+  rgo_release(&st);
+  return status;
+}
+
+int rgo_solve(int64_t n, int64_t m, const double *A, const double *Y, double tol,
+              int test_mode, int64_t r_max, double *X, int64_t *rank_out,
+              int64_t *basis_rows, uint8_t *indep, double *Ct_out, double *Pinv_out,
+              double *C_out, int64_t *rows_done) {
+  return rgo_solve_mut(n, m, A, Y, tol, test_mode, r_max, 0, X, rank_out, basis_rows, indep,
+                       Ct_out, Pinv_out, C_out, rows_done);
+}
+
+/*
+ * Batched form: B independent streams in the packed layout (instance b: rows
+ * A[elem_off[b] .. elem_off[b+1]) as n_b x m_b, targets Y[row_off[b] ..], solution
+ * X[x_off[b] .. x_off[b] + m_b)). Instances run in parallel over `threads` OpenMP
+ * threads (<= 0: all available). ranks (B) and status (B) may be NULL.
+ */
+int rgo_solve_batch(int64_t B, const int64_t *row_off, const int64_t *elem_off,
+                    const int64_t *x_off, const double *A, const double *Y, double tol,
+                    int test_mode, int threads, double *X, int64_t *ranks, int *status) {
+  if (B < 0 || !row_off || !elem_off || !x_off) return 1;
+  int bad = 0;
+#ifdef _OPENMP
+  if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+#endif
+  for (int64_t b = 0; b < B; ++b) {
+    int64_t n = row_off[b + 1] - row_off[b];
+    int64_t m = x_off[b + 1] - x_off[b];
+    int64_t rk = 0;
+    int st = 1;
+    if (m > 0 && (elem_off[b + 1] - elem_off[b]) == n * m)
+      st = rgo_solve(n, m, A + elem_off[b], Y + row_off[b], tol, test_mode, m, X + x_off[b],
+                     &rk, NULL, NULL, NULL, NULL, NULL, NULL);
+    if (ranks) ranks[b] = rk;
+    if (status) status[b] = st;
+    bad |= (st != 0);
+  }
+  return bad ? 1 : 0;
+}
+
+/* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
+int rgo_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

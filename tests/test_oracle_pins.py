@@ -1,0 +1,351 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test ties the FP64 oracle (oracle/rg_oracle.c) to something other than itself:
+exact rational arithmetic, an independent exact pseudoinverse route (Theorem 1 on an
+RREF factorization), textbook closed forms, numpy's SVD least squares, the Penrose
+equations and the values printed in the paper's Section 4.2 tables.
+"""
+import json
+import os
+from fractions import Fraction
+from math import comb
+
+import numpy as np
+import pytest
+
+from oracle import checks, exact, fp64
+from paper_2106_11594_gb300 import inputs
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+
+
+def pinv_by_unit_targets(A, tol):
+    """A^+ column by column: X(Y = e_j) = A^+ e_j (X is linear in Y, Section 1)."""
+    n = A.shape[0]
+    return np.stack([fp64.solve(A, np.eye(n)[j], tol=tol).X for j in range(n)], axis=1)
+
+
+def prefix_rank_trajectory(Afr):
+    """Definition of the rank trajectory: row i is independent iff
+    rank(A[:i+1]) > rank(A[:i]) (exact arithmetic)."""
+    out, prev = [], 0
+    for i in range(len(Afr)):
+        rk = exact.rank(Afr[:i + 1])
+        out.append(int(rk > prev))
+        prev = rk
+    return out
+
+
+INT_CASES = [
+    # (n, m, r, seed)
+    (6, 4, 2, 0),
+    (9, 5, 3, 1),
+    (7, 7, 7, 2),   # full rank square: r = m
+    (12, 6, 1, 3),  # rank one
+    (5, 8, 3, 4),   # n < m
+    (10, 3, 3, 5),  # full column rank
+]
+
+
+@pytest.mark.parametrize("n,m,r,seed", INT_CASES)
+def test_exact_alg1_equals_theorem1(n, m, r, seed):
+    """Exact Algorithm 1 and Theorem 1 on an RREF rank factorization give the same
+    A^+ Y (uniqueness of the Moore-Penrose inverse), and Algorithm 1's trajectory is the
+    prefix-rank definition."""
+    A, Y = inputs.integer_lowrank(n, m, r, seed)
+    A[n // 2] = 0.0                 # a zero row (dependent, K = 0)
+    A[-1] = A[0]                    # a duplicate row (dependent)
+    Afr, Yfr = exact.to_fractions(A), exact.to_fractions(Y)
+    res = exact.alg1(Afr, Yfr)
+    X_t1 = exact.lstsq_theorem1(Afr, Yfr)
+    assert res["X"] == X_t1
+    assert res["indep"] == prefix_rank_trajectory(Afr)
+    assert len(res["basis_rows"]) == exact.rank(Afr)
+    # dual basis identity Ct C^T = I exactly
+    Ct, C = res["Ct"], res["C"]
+    rr = len(C)
+    for i in range(rr):
+        for j in range(rr):
+            assert exact.dot(Ct[i], C[j]) == (1 if i == j else 0)
+
+
+@pytest.mark.parametrize("n,m,r,seed", INT_CASES)
+def test_fp64_oracle_matches_exact(n, m, r, seed):
+    A, Y = inputs.integer_lowrank(n, m, r, seed)
+    A[n // 2] = 0.0
+    A[-1] = A[0]
+    ref = exact.alg1(exact.to_fractions(A), exact.to_fractions(Y))
+    Xref = np.array([float(x) for x in ref["X"]])
+    res = fp64.solve(A, Y, tol=1e-10)
+    assert list(res.indep) == ref["indep"]
+    assert list(res.basis_rows) == ref["basis_rows"]
+    assert checks.rel_err(res.X, Xref) <= 1e-12
+    Pinv_ref = np.array([[float(x) for x in row] for row in ref["Pinv"]]).reshape(res.rank, res.rank)
+    assert np.allclose(res.Pinv, Pinv_ref, rtol=1e-10, atol=1e-12 * np.abs(Pinv_ref).max())
+
+
+def test_small_stream_prefix_exact():
+    """Workload 1's first 32 rows against exact Algorithm 1 on the exact product of its
+    FP64 factors (exactly rank 8): identical trajectory, X within kappa-scaled rounding."""
+    G1, G2, x_true, eps = inputs.factor_stream_factors(256, 64, 8, 1e-3, inputs.rng_for(1))
+    s = inputs.small_stream()
+    np.testing.assert_array_equal(s.A, G1 @ G2)
+    n = 32
+    Afr = exact.matmul(exact.to_fractions(G1[:n]), exact.to_fractions(G2))
+    Yfr = exact.to_fractions(s.Y[:n])
+    ref = exact.alg1(Afr, Yfr)
+    assert ref["indep"] == [1] * 8 + [0] * (n - 8)
+    res = fp64.solve(s.A[:n], s.Y[:n], tol=1e-10)
+    assert list(res.indep) == ref["indep"]
+    Xref = np.array([float(x) for x in ref["X"]])
+    assert checks.rel_err(res.X, Xref) <= 1e-11
+
+
+@pytest.mark.parametrize("n,m,r", [(40, 30, 7), (64, 64, 20), (30, 60, 12), (64, 16, 16)])
+def test_fp64_oracle_vs_svd_lstsq(n, m, r):
+    rng = inputs.rng_for(200, n * 1000 + m * 10 + r)
+    A = rng.standard_normal((n, r)) @ rng.standard_normal((r, m))
+    Y = rng.standard_normal(n)
+    res = fp64.solve(A, Y, tol=1e-10)
+    assert res.rank == r
+    sv = np.linalg.svd(A, compute_uv=False)
+    Xref = np.linalg.lstsq(A, Y, rcond=0.5 * sv[r - 1] / sv[0])[0]
+    assert checks.rel_err(res.X, Xref) <= 1e-10
+    Ap = np.linalg.pinv(A, rcond=0.5 * sv[r - 1] / sv[0])
+    assert checks.rel_err(pinv_by_unit_targets(A, 1e-10), Ap) <= 1e-9
+
+
+def test_penrose_and_invariants_small_stream():
+    s = inputs.small_stream()
+    res = fp64.solve(s.A, s.Y, tol=1e-10)
+    assert res.rank == 8
+    Ap = checks.pinv_from_factors(s.A, res.Ct, res.Pinv)
+    for rr in checks.penrose_residuals(s.A, Ap):
+        assert rr <= 1e-12
+    assert checks.rowspace_residual(res.X, res.Ct, res.C) <= 1e-12
+    assert checks.normal_eq_residual(s.A, res.X, s.Y) <= 1e-14
+    assert checks.dual_basis_residual(res.Ct, res.C) <= 1e-12
+    assert checks.pinv_gram_residual(s.A, res.Ct, res.Pinv) <= 1e-11
+    # the basis rows are input rows, stored verbatim (Algorithm 1 appends Gamma itself)
+    np.testing.assert_array_equal(res.C, s.A[res.basis_rows])
+
+
+@pytest.mark.parametrize("n,m,r", [(2048, 256, 32), (1024, 128, 64)])
+def test_rank_and_trajectory_equal_generator(n, m, r):
+    s = inputs.large_stream(n, m, r)
+    res = fp64.solve(s.A, s.Y, tol=1e-10)
+    assert res.rank == r
+    assert list(res.basis_rows) == list(range(r))
+    assert res.indep.sum() == r
+    Xref = np.linalg.lstsq(s.A, s.Y, rcond=1e-10)[0]
+    assert checks.rel_err(res.X, Xref) <= 1e-10
+
+
+def test_uneven_batch_sample_rank_and_batch_form():
+    bt = inputs.uneven_batch(B=4096, instances=[0, 1, 2, 3, 17, 101])
+    A, Y, ro, eo, xo = bt.packed()
+    X, ranks = fp64.solve_batch(A, Y, ro, eo, xo, tol=1e-10, threads=2)
+    n, m, r = inputs.uneven_batch_shapes()
+    for k, (b, s) in enumerate(zip([0, 1, 2, 3, 17, 101], bt.streams)):
+        assert ranks[k] == r[b]
+        one = fp64.solve(s.A, s.Y, tol=1e-10)
+        np.testing.assert_array_equal(X[xo[k]:xo[k + 1]], one.X)  # same code, same order
+
+
+# ---------------------------------------------------------------------------
+# Closed forms
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [4, 6, 8, 10])
+def test_pascal_exact_inverse(n):
+    """Section 4.2: with Fractions, rank-Greville returns the exact inverse of P(n).
+    Closed form: P = L L^T with L_ij = C(i, j), so P^-1 = L^-T L^-1 and
+    (L^-1)_ij = (-1)^(i-j) C(i, j)."""
+    A = inputs.pascal(n)
+    Linv = [[Fraction((-1) ** (i - j) * comb(i, j)) for j in range(n)] for i in range(n)]
+    Pinv_exact = exact.matmul(exact.transpose(Linv), Linv)
+    Afr = exact.to_fractions(A)
+    cols = []
+    for j in range(n):
+        e = [Fraction(int(i == j)) for i in range(n)]
+        cols.append(exact.alg1(Afr, e)["X"])
+    assert exact.transpose(cols) == Pinv_exact
+
+
+def test_identity_plus_ones_row_closed_form():
+    """A = [I_n; 1^T] (the example after the Theta(mn) corollary). Closed form:
+    A^+ = (I - 1 1^T / (n+1)) [I 1]."""
+    n = 6
+    A = np.vstack([np.eye(n), np.ones((1, n))])
+    ref = (np.eye(n) - np.ones((n, n)) / (n + 1)) @ np.hstack([np.eye(n), np.ones((n, 1))])
+    assert checks.rel_err(pinv_by_unit_targets(A, 1e-10), ref) <= 1e-14
+    Afr = exact.to_fractions(A)
+    for j in range(n + 1):
+        e = [Fraction(int(i == j)) for i in range(n + 1)]
+        X = exact.alg1(Afr, e)["X"]
+        ref_col = [Fraction(int(i == j)) - Fraction(1, n + 1) if j < n else Fraction(1, n + 1)
+                   for i in range(n)]
+        assert X == ref_col
+
+
+def test_full_column_rank_normal_equations():
+    """Full column rank (Section 1): X = (A^T A)^-1 A^T Y."""
+    rng = inputs.rng_for(201, 0)
+    A = rng.standard_normal((30, 10))
+    Y = rng.standard_normal(30)
+    res = fp64.solve(A, Y, tol=1e-10)
+    assert res.rank == 10
+    ref = np.linalg.solve(A.T @ A, A.T @ Y)
+    assert checks.rel_err(res.X, ref) <= 1e-13
+
+
+def test_square_full_rank_is_inverse():
+    rng = inputs.rng_for(202, 0)
+    A = rng.standard_normal((12, 12))
+    Y = rng.standard_normal(12)
+    res = fp64.solve(A, Y, tol=1e-10)
+    assert res.rank == 12 and list(res.indep) == [1] * 12
+    assert checks.rel_err(res.X, np.linalg.solve(A, Y)) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Golden values printed in the paper (Section 4.2 tables)
+# ---------------------------------------------------------------------------
+
+def test_golden_test_families_condition_numbers():
+    """The printed kappa_2 of each test family pins the generators of those families."""
+    g = GOLDEN["pascal"]
+    for n, k in zip(g["n"], g["kappa2"]):
+        assert abs(checks.kappa2(inputs.pascal(n)) / k - 1) < 0.01
+    g = GOLDEN["usv"]
+    for n, k in zip(g["n"], g["kappa2"]):
+        assert abs(checks.kappa2(inputs.usv(n)[0]) / k - 1) < 0.01
+    g = GOLDEN["kahan"]
+    for c, k in zip(g["c"], g["kappa2"]):
+        assert abs(checks.kappa2(inputs.kahan(g["n"], c)) / k - 1) < 0.01
+    assert abs(np.finfo(np.float64).eps / GOLDEN["machine_epsilon"]["eps_M"] - 1) < 0.01
+
+
+def test_golden_kahan_residuals():
+    """Table table_res_Kahan: rank-Greville residual errors on K(c, s), n = 100, with
+    the threshold below kappa^-1. Deterministic matrices; the oracle lands within a
+    factor 3 of every printed value."""
+    g = GOLDEN["kahan"]
+    for c, ref in zip(g["c"], g["res_rank_greville"]):
+        A = inputs.kahan(g["n"], c)
+        Ap = pinv_by_unit_targets(A, 1e-30)
+        res = checks.residual_error(Ap, A)
+        assert ref / 3 <= res <= ref * 3, (c, res, ref)
+
+
+def test_golden_pascal_metrics():
+    """Tables table_e_Pascal / table_res_Pascal: e and res of rank-Greville on P(n)
+    agree with the printed values to within a factor 30 (the paper's implementation
+    updates the pseudoinverse with a different operation order)."""
+    g = GOLDEN["pascal"]
+    for n, e_ref, r_ref in zip(g["n"], g["e_rank_greville"], g["res_rank_greville"]):
+        A = inputs.pascal(n)
+        Linv = np.array([[(-1) ** (i - j) * comb(i, j) for j in range(n)] for i in range(n)], float)
+        Ap = pinv_by_unit_targets(A, 1e-30)
+        e = checks.stability_factor(Ap, Linv.T @ Linv, A)
+        res = checks.residual_error(Ap, A)
+        assert e_ref / 30 <= e <= e_ref * 30, (n, e, e_ref)
+        assert r_ref / 30 <= res <= r_ref * 30, (n, res, r_ref)
+
+
+def test_golden_usv_metrics():
+    """Tables table_e_USV / table_res_USV (eps = 1e-8): seed-dependent, so the median
+    over 5 seeds must lie within a factor 30 of the printed value."""
+    g = GOLDEN["usv"]
+    for n, e_ref, r_ref in zip(g["n"], g["e_rank_greville"], g["res_rank_greville"]):
+        es, rs = [], []
+        for seed in range(5):
+            A, U, S, V = inputs.usv(n, seed)
+            Ap = pinv_by_unit_targets(A, g["eps"])
+            ref = V @ np.diag(1 / np.diag(S)) @ U.T
+            es.append(checks.stability_factor(Ap, ref, A))
+            rs.append(checks.residual_error(Ap, A))
+        assert e_ref / 30 <= np.median(es) <= e_ref * 30, (n, es, e_ref)
+        assert r_ref / 30 <= np.median(rs) <= r_ref * 30, (n, rs, r_ref)
+
+
+# ---------------------------------------------------------------------------
+# Threshold readings, capacity, degenerate inputs
+# ---------------------------------------------------------------------------
+
+def test_threshold_modes():
+    """REL: independent iff ||Gr|| > eps ||G||. PAPER (Eq. label_eq_eps): dependent iff
+    ||Gr|| < eps or ||Gr|| < eps ||G||. They differ only for ||G|| < 1."""
+    base = np.array([[1.0, 0.0, 0.0]])
+    tiny = np.array([[0.0, 1e-3, 0.0]])   # ||Gr|| = 1e-3 < eps = 1e-2 but > eps ||G|| = 1e-5
+    A = np.vstack([base, tiny])
+    Y = np.array([1.0, 2.0])
+    rel = fp64.solve(A, Y, tol=1e-2, test_mode=fp64.TEST_REL)
+    pap = fp64.solve(A, Y, tol=1e-2, test_mode=fp64.TEST_PAPER)
+    assert list(rel.indep) == [1, 1]
+    assert list(pap.indep) == [1, 0]
+
+
+def test_default_eps_formula():
+    """tol <= 0 selects eps = (m^2 r + m r + m) eps_M with r the rank before the row:
+    a perturbation just above / below that level is independent / dependent."""
+    m = 4
+    e1 = (m * m * 1 + m * 1 + m) * np.finfo(float).eps   # rank 1 before row 2
+    for scale, expect in [(3.0, 1), (0.3, 0)]:
+        A = np.array([[1.0, 0, 0, 0], [1.0, scale * e1, 0, 0]])
+        res = fp64.solve(A, np.array([1.0, 1.0]), tol=0.0)
+        assert list(res.indep) == [1, expect]
+
+
+def test_capacity_overflow_stops_before_row():
+    rng = inputs.rng_for(203, 0)
+    A = rng.standard_normal((6, 5))
+    res = fp64.solve(A, np.ones(6), tol=1e-10, r_max=3)
+    assert res.status == 4 and res.rows_done == 3 and res.rank == 3
+    ref = fp64.solve(A[:3], np.ones(3), tol=1e-10)
+    np.testing.assert_array_equal(res.X, ref.X)
+
+
+def test_degenerate_inputs():
+    # all-zero rows: rank stays 0, X stays 0
+    res = fp64.solve(np.zeros((5, 3)), np.ones(5), tol=1e-10)
+    assert res.rank == 0 and not res.X.any() and not res.indep.any()
+    # empty stream
+    res = fp64.solve(np.zeros((0, 3)), np.zeros(0), tol=1e-10)
+    assert res.rank == 0 and not res.X.any()
+    # a single row: X = y Gamma / ||Gamma||^2
+    g = np.array([[1.0, 2.0, 2.0]])
+    res = fp64.solve(g, np.array([9.0]), tol=1e-10)
+    np.testing.assert_allclose(res.X, 9.0 * g[0] / 9.0, rtol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Planted mistakes: every mutation of the oracle fails at least one pin
+# ---------------------------------------------------------------------------
+
+MUTATIONS = {
+    1: "wrong sign in the rejection (Gamma + C^T gamma)",
+    2: "dropped gamma K^T term in the dual-basis update",
+    3: "dropped 1 in the denominator 1 + gamma^T zeta",
+    4: "dropped P^-1 Sherman-Morrison update",
+    5: "transposed operand: gamma from C instead of Ct",
+    6: "wrong index into gamma in zeta = P^-1 gamma",
+    7: "wrong sign in the a-priori error y - Gamma^T X",
+}
+
+
+@pytest.mark.parametrize("mutation", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(mutation):
+    caught = []
+    # pin 1: exact rational run on integer data
+    for (n, m, r, seed) in INT_CASES[:3]:
+        A, Y = inputs.integer_lowrank(n, m, r, seed)
+        ref = exact.alg1(exact.to_fractions(A), exact.to_fractions(Y))
+        Xref = np.array([float(x) for x in ref["X"]])
+        res = fp64.solve(A, Y, tol=1e-10, mutation=mutation)
+        caught.append(list(res.indep) != ref["indep"] or checks.rel_err(res.X, Xref) > 1e-12)
+    # pin 2: SVD least squares on a stream with many dependent rows
+    s = inputs.large_stream(512, 64, 8)
+    res = fp64.solve(s.A, s.Y, tol=1e-10, mutation=mutation)
+    caught.append(checks.rel_err(res.X, np.linalg.lstsq(s.A, s.Y, rcond=1e-10)[0]) > 1e-10)
+    assert any(caught), MUTATIONS[mutation]
