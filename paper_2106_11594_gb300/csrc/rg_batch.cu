@@ -1,0 +1,445 @@
+// rg_batch.cu -- many independent rank-Greville streams of uneven shape in ONE persistent
+// kernel, plus the batched half of the C ABI.
+//
+// Each instance b (m_b columns, capacity r_max_b) owns its state (C, Ct or the FP32 copy
+// of Q, P^-1, w, basis rows) in one arena. Persistent CTAs pop instances from an atomic
+// work counter over an order sorted by estimated cost n_b m_b min(n_b, r_max_b),
+// longest first, and apply all rows of the instance with the same block phases as the
+// single-stream kernel (rg_core.cuh), the team being the CTA itself. Each CTA owns a
+// scratch slab sized for the largest instance. There is no spin-wait anywhere here.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "../../include/rg.h"
+#include "rg_core.cuh"
+#include "rg_host.h"
+
+namespace rg {
+
+struct BatchDev {
+  int B, mixed, test_mode, kb_max, ld_max, r_max_max, nmc_max;
+  double tol, tau_lo;
+  const int* m;               // B
+  const int* r_max;           // B
+  const long long* soff;      // B: byte offset of the instance state in `state`
+  const long long* xoff_def;  // B + 1: packed solution offsets by m_b
+  char* state;
+  int* ctrl;                  // B x CTRL_N
+  long long* rows_seen;       // B
+  char* scratch;              // one slab per CTA
+  size_t scratch_stride;
+  int* order;                 // B
+  int* queue;                 // [1]
+  int* bstatus;               // [1] OR of the instances' status bits
+};
+
+__host__ __device__ inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Instance state layout; fills S's state pointers when base != null. Returns bytes.
+__host__ __device__ inline size_t inst_layout(int m, int ld, int rmax, int mixed, char* base,
+                                              StreamDev* S) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + off : nullptr;
+    off = al256(off + bytes);
+    return p;
+  };
+  char* C = take((size_t)rmax * ld * 8);
+  char* Ct = mixed ? nullptr : take((size_t)rmax * ld * 8);
+  char* Qf = mixed ? take((size_t)rmax * ld * 4) : nullptr;
+  char* Pinv = take((size_t)rmax * rmax * 8);
+  char* w = take((size_t)rmax * 8);
+  char* basis = take((size_t)rmax * 8);
+  if (S) {
+    S->C = (double*)C;
+    S->Ct = (double*)Ct;
+    S->Qf = (float*)Qf;
+    S->Pinv = (double*)Pinv;
+    S->w = (double*)w;
+    S->basis_rows = (long long*)basis;
+  }
+  (void)m;
+  return off;
+}
+
+// Per-CTA scratch layout (sized with the batch maxima). Returns bytes.
+__host__ __device__ inline size_t scratch_layout(int kb, int ldm, int rmm, int nmcm, char* base,
+                                                 StreamDev* S) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + off : nullptr;
+    off = al256(off + bytes);
+    return p;
+  };
+  char* G = take((size_t)kb * rmm * 8);
+  char* sp = take((size_t)kb * nmcm * 8);
+  char* tp = take((size_t)kb * nmcm * 8);
+  char* s = take((size_t)kb * 8);
+  char* t = take((size_t)kb * 8);
+  char* rf = take((size_t)kb);
+  char* R = take((size_t)SLOW_MAX * ldm * 8);
+  char* Kv = take((size_t)SLOW_MAX * ldm * 8);
+  char* Gind = take((size_t)SLOW_MAX * rmm * 8);
+  char* alpha = take((size_t)SLOW_MAX * 8);
+  char* jind = take((size_t)SLOW_MAX * 4);
+  char* seg = take((size_t)3 * (SLOW_MAX + 2) * 4);
+  char* Zt = take((size_t)SB * rmm * 8);
+  char* M = take((size_t)SB * SB * 8);
+  char* Wt = take((size_t)SB * rmm * 8);
+  char* D = take((size_t)SB * 8);
+  char* aw = take((size_t)SB * 8);
+  if (S) {
+    S->G = (double*)G;
+    S->spart = (double*)sp;
+    S->tpart = (double*)tp;
+    S->s = (double*)s;
+    S->t = (double*)t;
+    S->rowflag = (uint8_t*)rf;
+    S->R = (double*)R;
+    S->Kv = (double*)Kv;
+    S->Gind = (double*)Gind;
+    S->alpha = (double*)alpha;
+    S->jind = (int*)jind;
+    S->seg = (int*)seg;
+    S->Zt = (double*)Zt;
+    S->M = (double*)M;
+    S->Wt = (double*)Wt;
+    S->D = (double*)D;
+    S->aw = (double*)aw;
+  }
+  return off;
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(NT, 2) batch_kernel(BatchDev D, const double* __restrict__ Gp,
+                                                   const int64_t* __restrict__ roff,
+                                                   const int64_t* __restrict__ eoff,
+                                                   const double* __restrict__ yp, uint8_t* indep) {
+  __shared__ int item;
+  StreamDev S{};
+  S.mixed = MIXED;
+  S.test_mode = D.test_mode;
+  S.tol = D.tol;
+  S.tau_lo = D.tau_lo;
+  S.kb_max = D.kb_max;
+  scratch_layout(D.kb_max, D.ld_max, D.r_max_max, D.nmc_max,
+                 D.scratch + (size_t)blockIdx.x * D.scratch_stride, &S);
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(D.queue, 1);
+    __syncthreads();
+    const int it = item;
+    __syncthreads();
+    if (it >= D.B) break;
+    const int b = D.order[it];
+    const int m = D.m[b];
+    const long long n = roff[b + 1] - roff[b];
+    if (n <= 0) continue;
+    if (eoff[b + 1] - eoff[b] != n * (long long)m) {
+      if (threadIdx.x == 0) {
+        atomicOr(D.ctrl + (size_t)b * CTRL_N + CTRL_STATUS, ST_BADARG);
+        atomicOr(D.bstatus, ST_BADARG);
+      }
+      continue;
+    }
+    S.m = m;
+    S.ld = (m + 3) / 4 * 4;
+    S.r_max = D.r_max[b];
+    S.nmc = (m + MC - 1) / MC;
+    inst_layout(m, S.ld, S.r_max, MIXED, D.state + D.soff[b], &S);
+    S.ctrl = D.ctrl + (size_t)b * CTRL_N;
+    S.rows_seen = D.rows_seen + b;
+    CallArgs A{Gp + eoff[b], yp + roff[b], n, indep ? indep + roff[b] : nullptr};
+    process_rows<CtaTeam, MIXED>(CtaTeam{}, S, A);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int st = ld_acquire_i32(S.ctrl + CTRL_STATUS);
+      if (st) atomicOr(D.bstatus, st);
+    }
+  }
+}
+
+// Longest-first order of the instances for this call (single CTA, bitonic sort in shared
+// memory for B <= 16384; larger batches keep index order). Also resets the work counter.
+__global__ void order_kernel(BatchDev D, const int64_t* __restrict__ roff) {
+  extern __shared__ unsigned long long keys[];
+  const int B = D.B;
+  if (threadIdx.x == 0) *D.queue = 0;
+  if (B > 16384) {
+    for (int b = threadIdx.x; b < B; b += blockDim.x) D.order[b] = b;
+    return;
+  }
+  int P = 1;
+  while (P < B) P <<= 1;
+  for (int b = threadIdx.x; b < P; b += blockDim.x) {
+    unsigned long long key = ~0ull;
+    if (b < B) {
+      const long long n = roff[b + 1] - roff[b];
+      const long long m = D.m[b];
+      const long long r = min((long long)D.r_max[b], max(n, 1ll));
+      double cost = (double)max(n, 0ll) * (double)m * (double)r;
+      const double cap = 8.796093022207e12;  // 2^43
+      if (cost > cap - 1.0) cost = cap - 1.0;
+      const unsigned long long c = (unsigned long long)cost;
+      key = ((((1ull << 43) - 1) - c) << 20) | (unsigned long long)b;  // descending cost
+    }
+    keys[b] = key;
+  }
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const unsigned long long a = keys[i], c = keys[l];
+          if ((a > c) == up) {
+            keys[i] = c;
+            keys[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int b = threadIdx.x; b < B; b += blockDim.x) D.order[b] = (int)(keys[b] & 0xFFFFFull);
+}
+
+__global__ void batch_solution_kernel(BatchDev D, double* X, const int64_t* xoff, int64_t* ranks) {
+  for (int b = blockIdx.x; b < D.B; b += gridDim.x) {
+    const int m = D.m[b];
+    StreamDev S{};
+    const int ld = (m + 3) / 4 * 4;
+    inst_layout(m, ld, D.r_max[b], D.mixed, D.state + D.soff[b], &S);
+    const int r = D.ctrl[(size_t)b * CTRL_N + CTRL_R];
+    const double* Bm = D.mixed ? S.C : S.Ct;
+    const long long x0 = xoff ? xoff[b] : D.xoff_def[b];
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      double acc = 0.0;
+      for (int i = 0; i < r; ++i) acc = fma(Bm[(size_t)i * ld + c], S.w[i], acc);
+      X[x0 + c] = acc;
+    }
+    if (ranks && threadIdx.x == 0) ranks[b] = r;
+  }
+}
+
+__global__ void batch_reset_kernel(BatchDev D, int kb0) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < D.B; b += gridDim.x * blockDim.x) {
+    int* c = D.ctrl + (size_t)b * CTRL_N;
+    for (int i = 0; i < CTRL_N; ++i) c[i] = 0;
+    c[CTRL_KB] = kb0;
+    D.rows_seen[b] = 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *D.bstatus = 0;
+}
+
+__global__ void batch_clear_status_kernel(BatchDev D) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < D.B; b += gridDim.x * blockDim.x)
+    D.ctrl[(size_t)b * CTRL_N + CTRL_STATUS] &= ST_TIMEOUT;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *D.bstatus &= ST_TIMEOUT;
+}
+
+}  // namespace rg
+
+using namespace rg;
+
+struct rg_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  BatchDev D{};
+  int grid = 0;
+  void* arena = nullptr;
+  std::vector<int> m, r_max;
+};
+
+namespace {
+int kb0_of(const BatchDev& D) { return std::min(KB_MIN, D.kb_max); }
+bool valid_batch(rg_batch* bt) { return bt && bt->arena; }
+}  // namespace
+
+extern "C" {
+
+rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol, int flags,
+                        const int64_t* r_max, void* cuda_stream) {
+  if (!out) return fail(RG_EINVAL, "rg_batch_init: out is NULL");
+  *out = nullptr;
+  if (B <= 0 || B > (1 << 20)) return fail(RG_EINVAL, "rg_batch_init: B = %lld out of range", (long long)B);
+  if (!m) return fail(RG_EINVAL, "rg_batch_init: m is NULL");
+  if (std::isnan(tol)) return fail(RG_EINVAL, "rg_batch_init: tol is NaN");
+  if (flags & ~(RG_MIXED | RG_TEST_PAPER)) return fail(RG_EINVAL, "rg_batch_init: unknown flags %d", flags);
+  rg_batch* bt = new (std::nothrow) rg_batch();
+  if (!bt) return fail(RG_ENOMEM, "rg_batch_init: host allocation failed");
+  bt->m.resize(B);
+  bt->r_max.resize(B);
+  int mmax = 0, rmm = 0;
+  for (int64_t b = 0; b < B; ++b) {
+    if (m[b] <= 0 || m[b] > (1 << 16)) {
+      delete bt;
+      return fail(RG_EINVAL, "rg_batch_init: m[%lld] = %lld out of range", (long long)b, (long long)m[b]);
+    }
+    long long rb = r_max ? r_max[b] : m[b];
+    if (rb <= 0 || rb > m[b]) rb = m[b];
+    bt->m[b] = (int)m[b];
+    bt->r_max[b] = (int)rb;
+    mmax = std::max(mmax, (int)m[b]);
+    rmm = std::max(rmm, (int)rb);
+  }
+  cudaError_t e = cudaGetDevice(&bt->device);
+  if (e != cudaSuccess) {
+    delete bt;
+    return cuda_fail(e, "rg_batch_init: no CUDA device");
+  }
+  bt->stream = (cudaStream_t)cuda_stream;
+  BatchDev& D = bt->D;
+  D.B = (int)B;
+  D.mixed = (flags & RG_MIXED) ? 1 : 0;
+  D.test_mode = (flags & RG_TEST_PAPER) ? 2 : 0;
+  D.tol = tol;
+  D.tau_lo = 1e-5;
+  D.ld_max = (mmax + 3) / 4 * 4;
+  D.r_max_max = rmm;
+  D.nmc_max = (mmax + MC - 1) / MC;
+  int kb = 256;
+  while (kb > 32 && (size_t)kb * rmm * 8 > (size_t)2 << 20) kb /= 2;
+  D.kb_max = kb;
+  int nsm = 0, per = 0;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, bt->device);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per, D.mixed ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>, NT, 0);
+  if (e != cudaSuccess || per <= 0) {
+    delete bt;
+    return e != cudaSuccess ? cuda_fail(e, "rg_batch_init: occupancy") : fail(RG_ECUDA, "rg_batch_init: no occupancy");
+  }
+  bt->grid = std::min<long long>((long long)nsm * per, B);
+  // host-side layout
+  std::vector<long long> soff(B), xoff(B + 1, 0);
+  size_t state_bytes = 0;
+  for (int64_t b = 0; b < B; ++b) {
+    soff[b] = (long long)state_bytes;
+    const int ld = (bt->m[b] + 3) / 4 * 4;
+    state_bytes += inst_layout(bt->m[b], ld, bt->r_max[b], D.mixed, nullptr, nullptr);
+    xoff[b + 1] = xoff[b] + bt->m[b];
+  }
+  StreamDev tmp{};
+  D.scratch_stride = al256(scratch_layout(D.kb_max, D.ld_max, D.r_max_max, D.nmc_max, nullptr, &tmp));
+  size_t off = 0;
+  auto place = [&](size_t bytes) {
+    const size_t o = off;
+    off = al256(off + bytes);
+    return o;
+  };
+  const size_t o_m = place(B * 4), o_r = place(B * 4), o_soff = place(B * 8), o_xoff = place((B + 1) * 8),
+               o_ctrl = place((size_t)B * CTRL_N * 4), o_rows = place(B * 8), o_order = place(B * 4),
+               o_q = place(4), o_bs = place(4), o_state = place(state_bytes),
+               o_scr = place(D.scratch_stride * (size_t)bt->grid);
+  e = cudaMalloc(&bt->arena, off);
+  if (e != cudaSuccess) {
+    delete bt;
+    return cuda_fail(e, "rg_batch_init: cudaMalloc");
+  }
+  char* base = (char*)bt->arena;
+  D.m = (int*)(base + o_m);
+  D.r_max = (int*)(base + o_r);
+  D.soff = (long long*)(base + o_soff);
+  D.xoff_def = (long long*)(base + o_xoff);
+  D.ctrl = (int*)(base + o_ctrl);
+  D.rows_seen = (long long*)(base + o_rows);
+  D.order = (int*)(base + o_order);
+  D.queue = (int*)(base + o_q);
+  D.bstatus = (int*)(base + o_bs);
+  D.state = base + o_state;
+  D.scratch = base + o_scr;
+  e = cudaMemsetAsync(bt->arena, 0, off, bt->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync((void*)D.m, bt->m.data(), B * 4, cudaMemcpyHostToDevice, bt->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync((void*)D.r_max, bt->r_max.data(), B * 4, cudaMemcpyHostToDevice, bt->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync((void*)D.soff, soff.data(), B * 8, cudaMemcpyHostToDevice, bt->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync((void*)D.xoff_def, xoff.data(), (B + 1) * 8, cudaMemcpyHostToDevice, bt->stream);
+  if (e == cudaSuccess) {
+    batch_reset_kernel<<<(B + 255) / 256, 256, 0, bt->stream>>>(D, kb0_of(D));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(bt->stream);  // host vectors go out of scope
+  if (e == cudaSuccess && B <= 16384)
+    e = cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8);
+  if (e != cudaSuccess) {
+    cudaFree(bt->arena);
+    delete bt;
+    return cuda_fail(e, "rg_batch_init: initialising the batch");
+  }
+  *out = bt;
+  return RG_OK;
+}
+
+rg_status rg_batch_add_rows(rg_batch* bt, const double* Gamma_packed, const int64_t* row_offsets,
+                            const int64_t* elem_offsets, const double* y_packed, uint8_t* indep_out) {
+  if (!valid_batch(bt)) return fail(RG_EINVAL, "rg_batch_add_rows: invalid batch");
+  if (!Gamma_packed || !row_offsets || !elem_offsets || !y_packed)
+    return fail(RG_EINVAL, "rg_batch_add_rows: NULL argument");
+  const BatchDev& D = bt->D;
+  int P = 1;
+  while (P < D.B) P <<= 1;
+  const size_t shm = D.B <= 16384 ? (size_t)P * 8 : 0;
+  order_kernel<<<1, 1024, shm, bt->stream>>>(D, row_offsets);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "rg_batch_add_rows: order kernel");
+  if (indep_out) {
+    // rows not applied keep 0xFF; the total row count is only known on the device, so the
+    // kernel writes every applied row and the rest are left as the caller initialised them
+  }
+  if (D.mixed)
+    batch_kernel<true><<<bt->grid, NT, 0, bt->stream>>>(D, Gamma_packed, row_offsets, elem_offsets,
+                                                        y_packed, indep_out);
+  else
+    batch_kernel<false><<<bt->grid, NT, 0, bt->stream>>>(D, Gamma_packed, row_offsets, elem_offsets,
+                                                         y_packed, indep_out);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "rg_batch_add_rows: launch");
+  return RG_OK;
+}
+
+rg_status rg_batch_solution(rg_batch* bt, double* X_packed, const int64_t* x_offsets, int64_t* ranks_out) {
+  if (!valid_batch(bt)) return fail(RG_EINVAL, "rg_batch_solution: invalid batch");
+  if (!X_packed) return fail(RG_EINVAL, "rg_batch_solution: X is NULL");
+  const int grid = std::min(bt->D.B, 4096);
+  batch_solution_kernel<<<grid, 256, 0, bt->stream>>>(bt->D, X_packed, x_offsets, ranks_out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "rg_batch_solution: launch");
+  return RG_OK;
+}
+
+rg_status rg_batch_sync(rg_batch* bt) {
+  if (!valid_batch(bt)) return fail(RG_EINVAL, "rg_batch_sync: invalid batch");
+  int bits = 0;
+  cudaError_t e = cudaMemcpyAsync(&bits, bt->D.bstatus, 4, cudaMemcpyDeviceToHost, bt->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(bt->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_batch_sync");
+  if (bits) {
+    batch_clear_status_kernel<<<(bt->D.B + 255) / 256, 256, 0, bt->stream>>>(bt->D);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "rg_batch_sync: clearing status");
+  }
+  return status_from_bits(bits);
+}
+
+rg_status rg_batch_reset(rg_batch* bt) {
+  if (!valid_batch(bt)) return fail(RG_EINVAL, "rg_batch_reset: invalid batch");
+  batch_reset_kernel<<<(bt->D.B + 255) / 256, 256, 0, bt->stream>>>(bt->D, kb0_of(bt->D));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "rg_batch_reset");
+  return RG_OK;
+}
+
+rg_status rg_batch_free(rg_batch* bt) {
+  if (!bt) return RG_OK;
+  cudaStreamSynchronize(bt->stream);
+  if (bt->arena) cudaFree(bt->arena);
+  delete bt;
+  return RG_OK;
+}
+
+}  // extern "C"

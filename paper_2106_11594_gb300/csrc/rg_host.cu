@@ -1,0 +1,355 @@
+// rg_host.cu -- host side of the C ABI declared in include/rg.h (single streams).
+//
+// Owns the device memory of a stream, validates arguments before anything is enqueued,
+// launches the kernels of rg_stream.cu on the state's stream and maps the device status
+// word to rg_status. There is no CPU fallback: every path runs the CUDA kernels.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/rg.h"
+#include "rg_host.h"
+#include "rg_internal.cuh"
+
+namespace rg {
+thread_local std::string g_last_error;
+
+rg_status fail(rg_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+rg_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear the sticky-free error so later calls start clean
+  return fail(e == cudaErrorMemoryAllocation ? RG_ENOMEM : RG_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+rg_status status_from_bits(int bits) {
+  if (bits & ST_TIMEOUT)
+    return fail(RG_ETIMEOUT, "a bounded device-side wait gave up; reset the state");
+  if (bits & ST_BADARG) return fail(RG_EINVAL, "inconsistent offsets found on the device");
+  if (bits & ST_NONFINITE)
+    return fail(RG_ENONFINITE, "a row or target was not finite (or a numerical breakdown "
+                               "made a Woodbury denominator non-positive); the rows from it "
+                               "on were not applied");
+  if (bits & ST_CAPACITY)
+    return fail(RG_ECAPACITY, "an independent row arrived at rank == r_max; the rows from it "
+                              "on were not applied");
+  return RG_OK;
+}
+
+__global__ void reset_kernel(int* ctrl, long long* rows_seen, int kb0) {
+  if (threadIdx.x < CTRL_N) ctrl[threadIdx.x] = 0;
+  if (threadIdx.x == 0) {
+    ctrl[CTRL_KB] = kb0;
+    *rows_seen = 0;
+  }
+}
+
+// Keeps the timeout bit (the state stays unusable until reset), clears the others.
+__global__ void clear_status_kernel(int* ctrl) {
+  ctrl[CTRL_STATUS] &= ST_TIMEOUT;
+}
+
+}  // namespace rg
+
+using namespace rg;
+
+struct rg_state {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  StreamDev S{};
+  int grid = 0;
+  void* arena = nullptr;  // one device allocation for everything
+  size_t arena_bytes = 0;
+  // staging for the host-buffer entry points (allocated on first use)
+  double* stage = nullptr;
+  uint8_t* stage_ind = nullptr;
+  long long stage_rows = 0;
+  double* xbuf = nullptr;
+};
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t n) {
+    off = align_up(off, 256);
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+// Lays out every device buffer of a stream; with base == nullptr it only measures.
+size_t carve(StreamDev& S, char* base) {
+  Carver cv{base};
+  const size_t ld = (size_t)S.ld, rm = (size_t)S.r_max, kb = (size_t)S.kb_max;
+  S.C = cv.take<double>(rm * ld);
+  S.Ct = S.mixed ? nullptr : cv.take<double>(rm * ld);
+  S.Qf = S.mixed ? cv.take<float>(rm * ld) : nullptr;
+  S.Pinv = cv.take<double>(rm * rm);
+  S.w = cv.take<double>(rm);
+  S.basis_rows = cv.take<long long>(rm);
+  S.rows_seen = cv.take<long long>(1);
+  S.ctrl = cv.take<int>(CTRL_N);
+  S.G = cv.take<double>(kb * rm);
+  S.spart = cv.take<double>(kb * (size_t)S.nmc);
+  S.tpart = cv.take<double>(kb * (size_t)S.nmc);
+  S.s = cv.take<double>(kb);
+  S.t = cv.take<double>(kb);
+  S.rowflag = cv.take<uint8_t>(kb);
+  S.R = cv.take<double>((size_t)SLOW_MAX * ld);
+  S.Kv = cv.take<double>((size_t)SLOW_MAX * ld);
+  S.Gind = cv.take<double>((size_t)SLOW_MAX * rm);
+  S.alpha = cv.take<double>(SLOW_MAX);
+  S.jind = cv.take<int>(SLOW_MAX);
+  S.seg = cv.take<int>(3 * (SLOW_MAX + 2));
+  S.Zt = cv.take<double>((size_t)SB * rm);
+  S.M = cv.take<double>((size_t)SB * SB);
+  S.Wt = cv.take<double>((size_t)SB * rm);
+  S.D = cv.take<double>(SB);
+  S.aw = cv.take<double>(SB);
+  return align_up(cv.off, 256);
+}
+
+bool valid_state(rg_state* st) { return st != nullptr && st->arena != nullptr; }
+
+rg_status pending_status(rg_state* st, bool clear) {
+  int bits = 0;
+  cudaError_t e = cudaMemcpyAsync(&bits, st->S.ctrl + CTRL_STATUS, sizeof(int),
+                                  cudaMemcpyDeviceToHost, st->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device status");
+  if (bits && clear) {
+    clear_status_kernel<<<1, 1, 0, st->stream>>>(st->S.ctrl);
+    cudaError_t e2 = cudaGetLastError();
+    if (e2 != cudaSuccess) return cuda_fail(e2, "clearing the device status");
+  }
+  return status_from_bits(bits);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rg_last_error(void) { return g_last_error.c_str(); }
+
+const char* rg_version(void) { return "rank-greville-gb300 0.1 (sm_103a)"; }
+
+rg_status rg_init(rg_state** out, int64_t m, double tol, int flags, int64_t r_max,
+                  void* cuda_stream) {
+  if (!out) return fail(RG_EINVAL, "rg_init: out is NULL");
+  *out = nullptr;
+  if (m <= 0 || m > (1 << 24)) return fail(RG_EINVAL, "rg_init: m = %lld out of range", (long long)m);
+  if (std::isnan(tol)) return fail(RG_EINVAL, "rg_init: tol is NaN");
+  if (flags & ~(RG_MIXED | RG_TEST_PAPER)) return fail(RG_EINVAL, "rg_init: unknown flags %d", flags);
+  if (r_max <= 0 || r_max > m) r_max = m;
+  rg_state* st = new (std::nothrow) rg_state();
+  if (!st) return fail(RG_ENOMEM, "rg_init: host allocation failed");
+  cudaError_t e = cudaGetDevice(&st->device);
+  if (e != cudaSuccess) {
+    delete st;
+    return cuda_fail(e, "rg_init: no CUDA device");
+  }
+  st->stream = (cudaStream_t)cuda_stream;
+  StreamDev& S = st->S;
+  S.m = (int)m;
+  S.ld = (int)align_up((size_t)m, 4);
+  S.r_max = (int)r_max;
+  S.mixed = (flags & RG_MIXED) ? 1 : 0;
+  S.test_mode = (flags & RG_TEST_PAPER) ? 2 : 0;
+  S.tol = tol;
+  S.tau_lo = 1e-5;
+  S.nmc = (int)((m + MC - 1) / MC);
+  // internal block: large enough to fill the GPU, bounded so the scratch stays small
+  long long kb = 4096;
+  while (kb > 256 && (double)kb * (double)r_max * 8.0 > 256.0 * (1 << 20)) kb /= 2;
+  S.kb_max = (int)kb;
+  st->arena_bytes = carve(S, nullptr);
+  e = cudaMalloc(&st->arena, st->arena_bytes);
+  if (e != cudaSuccess) {
+    delete st;
+    return cuda_fail(e, "rg_init: cudaMalloc of the state");
+  }
+  carve(S, (char*)st->arena);
+  e = stream_grid_size(S.mixed, &st->grid);
+  if (e != cudaSuccess || st->grid <= 0) {
+    cudaFree(st->arena);
+    delete st;
+    return e != cudaSuccess ? cuda_fail(e, "rg_init: occupancy query")
+                            : fail(RG_ECUDA, "rg_init: kernel cannot be made resident");
+  }
+  e = cudaMemsetAsync(st->arena, 0, st->arena_bytes, st->stream);
+  if (e == cudaSuccess) {
+    reset_kernel<<<1, 32, 0, st->stream>>>(S.ctrl, S.rows_seen, std::min(KB_MIN, S.kb_max));
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    cudaFree(st->arena);
+    delete st;
+    return cuda_fail(e, "rg_init: initialising the state");
+  }
+  *out = st;
+  return RG_OK;
+}
+
+rg_status rg_add_rows(rg_state* st, const double* Gamma, const double* y, int64_t k,
+                      uint8_t* indep_out) {
+  if (!valid_state(st)) return fail(RG_EINVAL, "rg_add_rows: invalid state");
+  if (k < 0) return fail(RG_EINVAL, "rg_add_rows: k = %lld < 0", (long long)k);
+  if (k == 0) return RG_OK;
+  if (!Gamma || !y) return fail(RG_EINVAL, "rg_add_rows: NULL rows or targets");
+  cudaError_t e = cudaSuccess;
+  if (indep_out) e = cudaMemsetAsync(indep_out, 0xFF, (size_t)k, st->stream);
+  if (e == cudaSuccess) e = launch_stream(st->S, Gamma, y, k, indep_out, st->grid, st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_add_rows: launch");
+  return RG_OK;
+}
+
+rg_status rg_add_rows_host(rg_state* st, const double* Gamma, const double* y, int64_t k,
+                           uint8_t* indep_out) {
+  if (!valid_state(st)) return fail(RG_EINVAL, "rg_add_rows_host: invalid state");
+  if (k < 0) return fail(RG_EINVAL, "rg_add_rows_host: k = %lld < 0", (long long)k);
+  if (k == 0) return RG_OK;
+  if (!Gamma || !y) return fail(RG_EINVAL, "rg_add_rows_host: NULL rows or targets");
+  const long long m = st->S.m;
+  if (!st->stage) {
+    long long rows = std::max<long long>(1, (64ll << 20) / (8 * (m + 1)));
+    cudaError_t e = cudaMalloc(&st->stage, (size_t)rows * (size_t)(m + 1) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&st->stage_ind, (size_t)rows);
+    if (e != cudaSuccess) return cuda_fail(e, "rg_add_rows_host: staging allocation");
+    st->stage_rows = rows;
+  }
+  for (long long c0 = 0; c0 < k; c0 += st->stage_rows) {
+    const long long n = std::min(st->stage_rows, (long long)k - c0);
+    double* dG = st->stage;
+    double* dy = st->stage + (size_t)st->stage_rows * (size_t)m;
+    cudaError_t e = cudaMemcpyAsync(dG, Gamma + (size_t)c0 * m, (size_t)n * m * 8,
+                                    cudaMemcpyHostToDevice, st->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dy, y + c0, (size_t)n * 8, cudaMemcpyHostToDevice, st->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "rg_add_rows_host: copy to device");
+    rg_status s = rg_add_rows(st, dG, dy, n, indep_out ? st->stage_ind : nullptr);
+    if (s != RG_OK) return s;
+    if (indep_out) {
+      e = cudaMemcpyAsync(indep_out + c0, st->stage_ind, (size_t)n, cudaMemcpyDeviceToHost,
+                          st->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "rg_add_rows_host: copy to host");
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_add_rows_host: synchronise");
+  return RG_OK;
+}
+
+rg_status rg_solution(rg_state* st, double* X, int64_t* rank_out) {
+  if (!valid_state(st)) return fail(RG_EINVAL, "rg_solution: invalid state");
+  if (!X) return fail(RG_EINVAL, "rg_solution: X is NULL");
+  cudaError_t e = launch_solution(st->S, X, st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_solution: launch");
+  if (rank_out) return rg_rank(st, rank_out);
+  return RG_OK;
+}
+
+rg_status rg_solution_host(rg_state* st, double* X, int64_t* rank_out) {
+  if (!valid_state(st)) return fail(RG_EINVAL, "rg_solution_host: invalid state");
+  if (!X) return fail(RG_EINVAL, "rg_solution_host: X is NULL");
+  if (!st->xbuf) {
+    cudaError_t e = cudaMalloc(&st->xbuf, (size_t)st->S.m * 8);
+    if (e != cudaSuccess) return cuda_fail(e, "rg_solution_host: allocation");
+  }
+  cudaError_t e = launch_solution(st->S, st->xbuf, st->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(X, st->xbuf, (size_t)st->S.m * 8, cudaMemcpyDeviceToHost, st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_solution_host");
+  if (rank_out) return rg_rank(st, rank_out);
+  e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_solution_host: synchronise");
+  return pending_status(st, true);
+}
+
+rg_status rg_rank(rg_state* st, int64_t* rank_out) {
+  if (!valid_state(st) || !rank_out) return fail(RG_EINVAL, "rg_rank: invalid argument");
+  int r = 0;
+  cudaError_t e = cudaMemcpyAsync(&r, st->S.ctrl + CTRL_R, sizeof(int), cudaMemcpyDeviceToHost,
+                                  st->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_rank");
+  *rank_out = r;
+  return pending_status(st, true);
+}
+
+rg_status rg_rows_seen(rg_state* st, int64_t* rows_out) {
+  if (!valid_state(st) || !rows_out) return fail(RG_EINVAL, "rg_rows_seen: invalid argument");
+  long long n = 0;
+  cudaError_t e = cudaMemcpyAsync(&n, st->S.rows_seen, sizeof(long long),
+                                  cudaMemcpyDeviceToHost, st->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_rows_seen");
+  *rows_out = n;
+  return RG_OK;
+}
+
+rg_status rg_sync(rg_state* st) {
+  if (!valid_state(st)) return fail(RG_EINVAL, "rg_sync: invalid state");
+  return pending_status(st, true);
+}
+
+rg_status rg_reset(rg_state* st) {
+  if (!valid_state(st)) return fail(RG_EINVAL, "rg_reset: invalid state");
+  reset_kernel<<<1, 32, 0, st->stream>>>(st->S.ctrl, st->S.rows_seen, std::min(KB_MIN, st->S.kb_max));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "rg_reset");
+  return RG_OK;
+}
+
+rg_status rg_export(rg_state* st, double* C, double* Ct, double* Pinv, double* w,
+                    int64_t* basis_rows, int64_t capacity, int64_t* rank_out) {
+  if (!valid_state(st)) return fail(RG_EINVAL, "rg_export: invalid state");
+  int64_t r = 0;
+  rg_status s = rg_rank(st, &r);
+  if (s != RG_OK && s != RG_ECAPACITY && s != RG_ENONFINITE) return s;
+  if (r > capacity) return fail(RG_EINVAL, "rg_export: rank %lld exceeds capacity %lld",
+                                (long long)r, (long long)capacity);
+  cudaError_t e = launch_export(st->S, C, Ct, Pinv, w, (long long*)basis_rows, st->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_export");
+  if (rank_out) *rank_out = r;
+  return RG_OK;
+}
+
+rg_status rg_set_stream(rg_state* st, void* cuda_stream) {
+  if (!valid_state(st)) return fail(RG_EINVAL, "rg_set_stream: invalid state");
+  cudaError_t e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_set_stream");
+  st->stream = (cudaStream_t)cuda_stream;
+  return RG_OK;
+}
+
+rg_status rg_free(rg_state* st) {
+  if (!st) return RG_OK;
+  cudaStreamSynchronize(st->stream);
+  if (st->arena) cudaFree(st->arena);
+  if (st->stage) cudaFree(st->stage);
+  if (st->stage_ind) cudaFree(st->stage_ind);
+  if (st->xbuf) cudaFree(st->xbuf);
+  delete st;
+  return RG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,25 @@
+// rg_host.h -- launch helpers shared between the host files of librg.so (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+
+#include "../../include/rg.h"
+#include "rg_internal.cuh"
+
+namespace rg {
+
+rg_status fail(rg_status code, const char* fmt, ...);
+rg_status cuda_fail(cudaError_t e, const char* what);
+rg_status status_from_bits(int bits);
+
+cudaError_t launch_stream(const StreamDev& S, const double* Gamma, const double* y, long long k,
+                          uint8_t* indep, int grid, cudaStream_t stream);
+cudaError_t stream_grid_size(int mixed, int* grid);
+cudaError_t launch_solution(const StreamDev& S, double* X, cudaStream_t stream);
+cudaError_t launch_export(const StreamDev& S, double* C, double* Ct, double* Pinv, double* w,
+                          long long* basis, cudaStream_t stream);
+
+}  // namespace rg

@@ -1,0 +1,158 @@
+// rg_internal.cuh -- device-side state layout and helpers shared by the CUDA kernels of
+// librg.so. Not part of the public ABI (include/rg.h is).
+#pragma once
+
+#include <cfloat>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rg {
+
+constexpr int NT = 256;          // threads per CTA in every kernel
+constexpr int NWARP = NT / 32;   // warps per CTA
+constexpr int SB = 32;           // rows per blocked Sherman-Morrison (Woodbury) step
+constexpr int SLOW_MAX = 32;     // rows per sequential rank-change section
+constexpr int KB_MIN = 64;       // internal block size right after a rank change
+constexpr int JW = 4;            // observation rows per warp tile in the gamma phase
+constexpr int RJ = 4;            // observation rows per CTA item in the rejection phase
+constexpr int MC = NT / RJ;      // columns per CTA item in the rejection phase (64)
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // bounded waits: 2 s
+
+// Device status bits (mapped to rg_status on the host).
+enum : int { ST_NONFINITE = 1, ST_CAPACITY = 2, ST_TIMEOUT = 4, ST_BADARG = 8 };
+
+// Control words of one stream (device memory).
+enum : int {
+  CTRL_R = 0,          // current rank r
+  CTRL_STATUS = 1,     // sticky error bits
+  CTRL_BAR_COUNT = 2,  // grid barrier arrival counter
+  CTRL_BAR_GEN = 3,    // grid barrier generation
+  CTRL_KB = 4,         // adaptive internal block size
+  CTRL_Q0 = 5,         // block plan: first row that needs the sequential section
+  CTRL_NSEG = 6,       // block plan: number of segments in the sequential section
+  CTRL_APPLIED = 7,    // block plan: rows of the block that were applied
+  CTRL_RNEW = 8,       // block plan: rank after the block
+  CTRL_NIND = 9,       // block plan: independent rows found in the block
+  CTRL_N = 16
+};
+
+// Segment kinds of the sequential section's plan.
+enum : int { SEG_DEP = 0, SEG_IND = 1 };
+
+// Everything a kernel needs to know about one stream. Plain pointers into device
+// memory owned by the host-side rg_state. Two algebraic variants:
+//  * general (FP64 mode): C = selected observation rows, Ct = dual basis
+//    (Ct C^T = I), Algorithm 1 of the paper;
+//  * orthonormal (mixed mode): C = Q with orthonormal rows spanning the same space
+//    (Section 2.2, alpha = 1/||Gamma_r||), so the dual basis is Q itself; a FP32 copy
+//    Qf feeds the FP32 projections.
+struct StreamDev {
+  int m, ld, r_max, kb_max;
+  int mixed;      // 1: orthonormal variant with FP32 projections
+  int test_mode;  // 0 REL, 2 PAPER
+  double tol;     // <= 0: paper default (m^2 r + m r + m) eps_M
+  double tau_lo;  // mixed mode: FP32 relative-rejection floor below which rows are dependent
+  double* C;      // r_max x ld
+  double* Ct;     // r_max x ld (general variant only)
+  float* Qf;      // r_max x ld (mixed only)
+  double* Pinv;   // r_max x r_max
+  double* w;      // r_max: X = Ct^T w
+  long long* basis_rows;  // r_max
+  long long* rows_seen;   // [1]
+  int* ctrl;              // CTRL_N ints
+  // scratch of one internal block
+  double* G;      // kb_max x r_max: gamma of each row of the block (row-major by row)
+  double* spart;  // kb_max x nmc: partial ||Gamma_r||^2 per column chunk
+  double* tpart;  // kb_max x nmc: partial ||Gamma||^2 per column chunk
+  int nmc;        // column chunks = ceil(m / MC)
+  double* s;      // kb_max
+  double* t;      // kb_max
+  uint8_t* rowflag;   // kb_max: 1 = dependent, 2 = independent (per row of the block)
+  double* R;      // SLOW_MAX x ld: FP64 rejections of the sequential section
+  double* Kv;     // SLOW_MAX x ld: new dual rows K (general) or new Q rows (orthonormal)
+  double* Gind;   // SLOW_MAX x r_max: gamma (fixed up) of each independent row
+  double* alpha;  // SLOW_MAX: orthonormal scale 1/||Gamma_r|| of each independent row
+  int* jind;      // SLOW_MAX: block row of each independent row
+  int* seg;       // 3 ints per segment: kind, first row, count
+  double* Zt;     // SB x r_max: zeta_j = P^-1 gamma_j of the current Woodbury step
+  double* M;      // SB x SB: I + G^T P^-1 G
+  double* Wt;     // SB x r_max: L^-1 Z^T
+  double* D;      // SB: a-priori errors y - gamma^T w
+  double* aw;     // SB: M^-1 D
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_acquire_i32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident). The wait is
+// bounded: after WAIT_LIMIT_NS the CTA records ST_TIMEOUT and returns false instead of
+// spinning forever. Works across launches because the last arriver resets the counter.
+__device__ __forceinline__ bool grid_barrier(int* ctrl) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    unsigned* count = reinterpret_cast<unsigned*>(ctrl + CTRL_BAR_COUNT);
+    unsigned* gen = reinterpret_cast<unsigned*>(ctrl + CTRL_BAR_GEN);
+    const unsigned g = ld_acquire_u32(gen);
+    __threadfence();
+    const unsigned prev = atomicAdd(count, 1u);
+    if (prev == gridDim.x - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire_u32(gen) == g) {
+        if (global_ns() - t0 > WAIT_LIMIT_NS) {
+          atomicOr(ctrl + CTRL_STATUS, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(40);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Rank test of Eq. label_eq_eps in squared form. s = ||Gamma_r||^2, t = ||Gamma||^2.
+__device__ __forceinline__ bool is_independent(double s, double t, int r, int m, double tol,
+                                               int test_mode) {
+  double eps = tol;
+  if (!(eps > 0.0)) {
+    const double md = (double)m, rd = (double)r;
+    eps = (md * md * rd + md * rd + md) * DBL_EPSILON;
+  }
+  const double e2 = eps * eps;
+  if (test_mode == 2) return !(s < e2 || s < e2 * t);
+  return s > e2 * t;
+}
+
+}  // namespace rg

@@ -1,0 +1,219 @@
+"""Thin Python binding of librg.so (include/rg.h): argument marshalling only.
+
+Every function here calls the C ABI of the same name; all arithmetic runs in the CUDA
+kernels of librg.so. PyTorch provides device memory and the current CUDA stream. There
+is no CPU fallback: if the library cannot be built or loaded, or no GPU is present, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+RG_OK, RG_EINVAL, RG_ENOMEM, RG_ECUDA, RG_ECAPACITY, RG_ENONFINITE, RG_ETIMEOUT = range(7)
+RG_FP64, RG_MIXED = 0, 1
+RG_TEST_REL, RG_TEST_PAPER = 0, 2
+
+STATUS_NAMES = {0: "RG_OK", 1: "RG_EINVAL", 2: "RG_ENOMEM", 3: "RG_ECUDA", 4: "RG_ECAPACITY",
+                5: "RG_ENONFINITE", 6: "RG_ETIMEOUT"}
+
+HEADER = os.path.join(_build.ROOT, "include", "rg.h")
+
+_lib = None
+
+
+class RGError(RuntimeError):
+    def __init__(self, code: int, func: str, msg: str):
+        super().__init__(f"{func} -> {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def declared_functions():
+    """Names of the functions include/rg.h declares."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:rg_status|const char\*)\s+(rg_\w+)\s*\(", txt, re.M)))
+
+
+def lib(build: bool = True):
+    """Load librg.so (building it first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    L = ctypes.CDLL(path)
+    vp, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "rg_init": [vp, i64, f64, i32, i64, vp],
+        "rg_add_rows": [vp, vp, vp, i64, vp],
+        "rg_add_rows_host": [vp, vp, vp, i64, vp],
+        "rg_solution": [vp, vp, vp],
+        "rg_solution_host": [vp, vp, vp],
+        "rg_rank": [vp, vp],
+        "rg_rows_seen": [vp, vp],
+        "rg_sync": [vp],
+        "rg_reset": [vp],
+        "rg_export": [vp, vp, vp, vp, vp, vp, i64, vp],
+        "rg_set_stream": [vp, vp],
+        "rg_free": [vp],
+        "rg_batch_init": [vp, i64, vp, f64, i32, vp, vp],
+        "rg_batch_add_rows": [vp, vp, vp, vp, vp, vp],
+        "rg_batch_solution": [vp, vp, vp, vp],
+        "rg_batch_sync": [vp],
+        "rg_batch_reset": [vp],
+        "rg_batch_free": [vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.rg_last_error.restype = ctypes.c_char_p
+    L.rg_version.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(code: int, func: str):
+    if code != RG_OK:
+        raise RGError(code, func, lib().rg_last_error().decode())
+
+
+def _ptr(t):
+    """Device or host pointer of a tensor / numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    return t.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        raise RGError(RG_ECUDA, "rg", "no CUDA device: librg has no CPU fallback")
+
+
+class RankGreville:
+    """One recursive least-squares stream (rg_init / rg_add_rows / rg_solution / rg_free)."""
+
+    def __init__(self, m: int, tol: float = 1e-10, mode: int = RG_FP64,
+                 test: int = RG_TEST_REL, r_max: int = 0, stream=None):
+        _need_cuda()
+        self.m = int(m)
+        self.flags = int(mode) | int(test)
+        self._h = ctypes.c_void_p()
+        self._stream = stream
+        _check(lib().rg_init(ctypes.byref(self._h), self.m, float(tol), self.flags, int(r_max),
+                             _stream(stream)), "rg_init")
+
+    def add_rows(self, Gamma, y, indep=None):
+        """Gamma: (k, m) float64 CUDA tensor (contiguous); y: (k,); indep: (k,) uint8 or None."""
+        k = 0 if Gamma.numel() == 0 else Gamma.shape[0]
+        _check(lib().rg_add_rows(self._h, _ptr(Gamma), _ptr(y), k, _ptr(indep)), "rg_add_rows")
+
+    def add_rows_host(self, Gamma, y, indep=None):
+        """Same with host (numpy) buffers; copies happen inside the call."""
+        k = Gamma.shape[0]
+        _check(lib().rg_add_rows_host(self._h, _ptr(Gamma), _ptr(y), k, _ptr(indep)),
+               "rg_add_rows_host")
+
+    def solution(self, X, with_rank: bool = True):
+        r = ctypes.c_int64(0)
+        _check(lib().rg_solution(self._h, _ptr(X), ctypes.byref(r) if with_rank else None),
+               "rg_solution")
+        return int(r.value) if with_rank else None
+
+    def solution_host(self, X):
+        r = ctypes.c_int64(0)
+        _check(lib().rg_solution_host(self._h, _ptr(X), ctypes.byref(r)), "rg_solution_host")
+        return int(r.value)
+
+    def rank(self) -> int:
+        r = ctypes.c_int64(0)
+        _check(lib().rg_rank(self._h, ctypes.byref(r)), "rg_rank")
+        return int(r.value)
+
+    def rows_seen(self) -> int:
+        r = ctypes.c_int64(0)
+        _check(lib().rg_rows_seen(self._h, ctypes.byref(r)), "rg_rows_seen")
+        return int(r.value)
+
+    def sync(self):
+        _check(lib().rg_sync(self._h), "rg_sync")
+
+    def reset(self):
+        _check(lib().rg_reset(self._h), "rg_reset")
+
+    def export(self, C=None, Ct=None, Pinv=None, w=None, basis_rows=None, capacity=None):
+        cap = self.m if capacity is None else capacity
+        r = ctypes.c_int64(0)
+        _check(lib().rg_export(self._h, _ptr(C), _ptr(Ct), _ptr(Pinv), _ptr(w), _ptr(basis_rows),
+                               int(cap), ctypes.byref(r)), "rg_export")
+        return int(r.value)
+
+    def close(self):
+        if self._h:
+            lib().rg_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class RankGrevilleBatch:
+    """B independent streams of uneven shape (rg_batch_*)."""
+
+    def __init__(self, m_list, tol: float = 1e-10, mode: int = RG_FP64, test: int = RG_TEST_REL,
+                 r_max_list=None, stream=None):
+        import numpy as np
+        _need_cuda()
+        self.m = np.ascontiguousarray(m_list, dtype=np.int64)
+        self.B = int(self.m.shape[0])
+        rm = None if r_max_list is None else np.ascontiguousarray(r_max_list, dtype=np.int64)
+        self._h = ctypes.c_void_p()
+        _check(lib().rg_batch_init(ctypes.byref(self._h), self.B, _ptr(self.m), float(tol),
+                                   int(mode) | int(test), _ptr(rm), _stream(stream)),
+               "rg_batch_init")
+
+    def add_rows(self, Gamma_packed, row_offsets, elem_offsets, y_packed, indep=None):
+        _check(lib().rg_batch_add_rows(self._h, _ptr(Gamma_packed), _ptr(row_offsets),
+                                       _ptr(elem_offsets), _ptr(y_packed), _ptr(indep)),
+               "rg_batch_add_rows")
+
+    def solution(self, X_packed, x_offsets=None, ranks=None):
+        _check(lib().rg_batch_solution(self._h, _ptr(X_packed), _ptr(x_offsets), _ptr(ranks)),
+               "rg_batch_solution")
+
+    def sync(self):
+        _check(lib().rg_batch_sync(self._h), "rg_batch_sync")
+
+    def reset(self):
+        _check(lib().rg_batch_reset(self._h), "rg_batch_reset")
+
+    def close(self):
+        if self._h:
+            lib().rg_batch_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

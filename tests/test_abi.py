@@ -1,0 +1,36 @@
+"""The C ABI library builds for sm_103a, loads, and exports every symbol that
+include/rg.h declares (no GPU needed: nothing here calls into the device)."""
+import ctypes
+import os
+import re
+import subprocess
+
+from paper_2106_11594_gb300 import build, rg
+
+
+def test_header_declares_the_boundary():
+    names = rg.declared_functions()
+    for fn in ["rg_init", "rg_add_rows", "rg_solution", "rg_free", "rg_batch_init",
+               "rg_batch_add_rows", "rg_batch_solution", "rg_batch_free", "rg_last_error"]:
+        assert fn in names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    assert os.path.exists(path)
+    L = ctypes.CDLL(path)
+    for name in rg.declared_functions():
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (rg_\w+)$", out, re.M))
+    assert set(rg.declared_functions()) <= exported
+
+
+def test_library_is_built_for_sm_103a_only():
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_version_string_without_gpu():
+    L = rg.lib()
+    assert b"sm_103a" in L.rg_version()
+    assert L.rg_last_error() == b""

@@ -1,0 +1,221 @@
+"""Single-stream parity: CUDA path (through the C ABI) vs the CPU oracle.
+
+Bar: FP64 mode ||X - X_ref|| / ||X_ref|| <= 1e-10, mixed mode <= 1e-4 (the tolerances the
+target states), and identical rank trajectories (per-row independence flags and basis-row
+indices compared as integer arrays)."""
+import numpy as np
+import pytest
+
+from gpu_helpers import run_stream, torch_cuda
+from oracle import checks, fp64
+from paper_2106_11594_gb300 import inputs, rg
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOLMIX = 1e-4
+
+
+def assert_parity(g, o, tol, compare_state=True):
+    assert g["rank"] == o.rank
+    np.testing.assert_array_equal(g["indep"], o.indep)
+    np.testing.assert_array_equal(g["basis"], o.basis_rows)
+    assert checks.rel_err(g["X"], o.X) <= tol, checks.rel_err(g["X"], o.X)
+    if compare_state:
+        np.testing.assert_array_equal(g["C"], o.C)  # the basis rows are input rows, verbatim
+        assert checks.rel_err(g["Ct"], o.Ct) <= 1e3 * tol
+        assert checks.rel_err(g["Pinv"], o.Pinv) <= 1e3 * tol
+
+
+@pytest.mark.parametrize("k", [1, 3, 32, 256])
+def test_small_stream_fp64(k):
+    s = inputs.small_stream()
+    o = fp64.solve(s.A, s.Y, tol=1e-10)
+    g = run_stream(s.A, s.Y, k)
+    assert_parity(g, o, TOL64)
+
+
+@pytest.mark.parametrize("k", [1, 32, 256])
+def test_small_stream_mixed(k):
+    s = inputs.small_stream()
+    o = fp64.solve(s.A, s.Y, tol=1e-10)
+    g = run_stream(s.A, s.Y, k, mode=rg.RG_MIXED)
+    assert g["rank"] == o.rank
+    np.testing.assert_array_equal(g["indep"], o.indep)
+    np.testing.assert_array_equal(g["basis"], o.basis_rows)
+    assert checks.rel_err(g["X"], o.X) <= TOLMIX
+    # orthonormal variant: the exported basis has orthonormal rows spanning span(C)
+    Q = g["C"]
+    assert np.linalg.norm(Q @ Q.T - np.eye(g["rank"])) <= 1e-10
+    assert np.linalg.norm(o.C - (o.C @ Q.T) @ Q) <= 1e-10 * np.linalg.norm(o.C)
+
+
+@pytest.mark.parametrize("n,m,r,k", [(4096, 1024, 64, 32), (4096, 1024, 64, 4096),
+                                     (3001, 1000, 48, 1000), (2500, 333, 40, 77)])
+def test_large_stream_fp64(n, m, r, k):
+    s = inputs.large_stream(n, m, r)
+    o = fp64.solve(s.A, s.Y, tol=1e-10)
+    g = run_stream(s.A, s.Y, k)
+    assert_parity(g, o, TOL64)
+
+
+@pytest.mark.parametrize("n,m,r,k", [(4096, 1024, 64, 32), (3001, 1000, 48, 3001)])
+def test_large_stream_mixed(n, m, r, k):
+    s = inputs.large_stream(n, m, r)
+    o = fp64.solve(s.A, s.Y, tol=1e-10)
+    g = run_stream(s.A, s.Y, k, mode=rg.RG_MIXED)
+    assert g["rank"] == o.rank
+    np.testing.assert_array_equal(g["indep"], o.indep)
+    np.testing.assert_array_equal(g["basis"], o.basis_rows)
+    assert checks.rel_err(g["X"], o.X) <= TOLMIX
+
+
+def test_full_size_large_stream_fp64_k32():
+    """The benchmark's workload at full size (n=65536, m=1024, r=64) in the benchmark's
+    launch configuration (32 rows per call): full oracle comparison plus properties."""
+    s = inputs.large_stream()
+    g = run_stream(s.A, s.Y, 32, export=True)
+    o = fp64.solve(s.A, s.Y, tol=1e-10)
+    assert_parity(g, o, TOL64, compare_state=False)
+    assert g["rank"] == 64 and list(g["basis"]) == list(range(64))
+    assert checks.normal_eq_residual(s.A, g["X"], s.Y) <= 1e-13
+    assert checks.rowspace_residual(g["X"], g["Ct"], g["C"]) <= 1e-12
+
+
+def test_full_size_large_stream_mixed_one_call():
+    s = inputs.large_stream()
+    g = run_stream(s.A, s.Y, s.n, mode=rg.RG_MIXED, export=False)
+    assert g["rank"] == 64
+    np.testing.assert_array_equal(np.nonzero(g["indep"])[0], np.arange(64))
+    o = fp64.solve(s.A, s.Y, tol=1e-10)
+    assert checks.rel_err(g["X"], o.X) <= TOLMIX
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_zero_and_duplicate_rows():
+    s = inputs.large_stream(600, 96, 12)
+    A = s.A.copy()
+    A[5] = 0.0
+    A[40:44] = 0.0
+    A[100] = A[3]
+    A[200] = A[0]
+    o = fp64.solve(A, s.Y, tol=1e-10)
+    for k in (1, 16, 600):
+        assert_parity(run_stream(A, s.Y, k), o, TOL64)
+
+
+def test_all_zero_stream_and_empty_call():
+    torch, dev = torch_cuda()
+    A = np.zeros((50, 7))
+    g = run_stream(A, np.ones(50), 8)
+    assert g["rank"] == 0 and not g["X"].any() and not g["indep"].any()
+    st = rg.RankGreville(7)
+    st.add_rows(torch.zeros((0, 7), dtype=torch.float64, device=dev),
+                torch.zeros(0, dtype=torch.float64, device=dev))
+    assert st.rank() == 0 and st.rows_seen() == 0
+
+
+def test_single_column():
+    A = np.array([[2.0], [0.0], [4.0], [-1.0]])
+    Y = np.array([1.0, 5.0, 2.0, 3.0])
+    o = fp64.solve(A, Y, tol=1e-10)
+    assert_parity(run_stream(A, Y, 1), o, TOL64)
+    assert_parity(run_stream(A, Y, 4), o, TOL64)
+
+
+@pytest.mark.parametrize("mode,tol", [(rg.RG_FP64, TOL64), (rg.RG_MIXED, TOLMIX)])
+def test_full_rank_square_and_wide(mode, tol):
+    rng = inputs.rng_for(300, 0)
+    A = rng.standard_normal((48, 48))
+    Y = rng.standard_normal(48)
+    g = run_stream(A, Y, 16, mode=mode)
+    assert g["rank"] == 48
+    assert checks.rel_err(g["X"], np.linalg.solve(A, Y)) <= tol * 100
+    W = rng.standard_normal((20, 90))  # n < m: minimum-norm interpolation
+    g = run_stream(W, Y[:20], 7, mode=mode)
+    assert g["rank"] == 20
+    assert checks.rel_err(g["X"], np.linalg.pinv(W) @ Y[:20]) <= tol
+
+
+def test_capacity_overflow():
+    rng = inputs.rng_for(301, 0)
+    A = rng.standard_normal((40, 12)) @ np.diag(np.ones(12))
+    Y = rng.standard_normal(40)
+    o = fp64.solve(A, Y, tol=1e-10, r_max=5)
+    assert o.status == 4 and o.rows_done == 5
+    g = run_stream(A, Y, 40, r_max=5, export=False, raise_errors=False)
+    assert g["err"] is not None and g["err"].code == rg.RG_ECAPACITY
+    assert g["rows_seen"] == 5 and g["rank"] == 5
+    assert checks.rel_err(g["X"], o.X) <= TOL64
+    assert (g["indep"][5:] == 0xFF).all()
+
+
+def test_nonfinite_row_stops_and_state_survives():
+    torch, dev = torch_cuda()
+    s = inputs.large_stream(300, 64, 10)
+    A = s.A.copy()
+    A[77, 3] = np.nan
+    st = rg.RankGreville(64)
+    At = torch.from_numpy(A).to(dev)
+    Yt = torch.from_numpy(s.Y).to(dev)
+    st.add_rows(At[:100], Yt[:100])
+    with pytest.raises(rg.RGError) as ei:
+        st.sync()
+    assert ei.value.code == rg.RG_ENONFINITE
+    assert st.rows_seen() == 77
+    X = torch.empty(64, dtype=torch.float64, device=dev)
+    st.solution(X)
+    o = fp64.solve(A[:77], s.Y[:77], tol=1e-10)
+    assert checks.rel_err(X.cpu().numpy(), o.X) <= TOL64
+    # the error was reported once; the stream continues with clean rows
+    st.add_rows(At[78:300], Yt[78:300])
+    st.solution(X)
+    keep = np.r_[0:77, 78:300]
+    o2 = fp64.solve(A[keep], s.Y[keep], tol=1e-10)
+    assert checks.rel_err(X.cpu().numpy(), o2.X) <= TOL64
+
+
+def test_paper_threshold_mode_and_default_eps():
+    s = inputs.large_stream(400, 64, 9)
+    A = s.A * 1e-3  # row norms < 1: PAPER and REL differ in principle
+    for test in (rg.RG_TEST_REL, rg.RG_TEST_PAPER):
+        for tol in (1e-10, 0.0):
+            o = fp64.solve(A, s.Y, tol=tol, test_mode=test)
+            assert_parity(run_stream(A, s.Y, 50, tol=tol, test=test), o, TOL64)
+
+
+def test_reset_rerun_is_bit_identical_and_host_api_matches():
+    torch, dev = torch_cuda()
+    s = inputs.large_stream(2000, 256, 24)
+    g1 = run_stream(s.A, s.Y, 64, export=False)
+    st = g1["state"]
+    st.reset()
+    At = torch.from_numpy(s.A).to(dev)
+    Yt = torch.from_numpy(s.Y).to(dev)
+    for j0 in range(0, 2000, 64):
+        st.add_rows(At[j0:j0 + 64], Yt[j0:j0 + 64])
+    X = torch.empty(256, dtype=torch.float64, device=dev)
+    st.solution(X)
+    np.testing.assert_array_equal(X.cpu().numpy(), g1["X"])
+    # host-buffer entry points
+    st.reset()
+    ind = np.zeros(2000, dtype=np.uint8)
+    for j0 in range(0, 2000, 64):
+        st.add_rows_host(s.A[j0:j0 + 64], s.Y[j0:j0 + 64], ind[j0:j0 + 64])
+    Xh = np.empty(256)
+    assert st.solution_host(Xh) == 24
+    np.testing.assert_array_equal(Xh, g1["X"])
+    np.testing.assert_array_equal(ind, g1["indep"])
+
+
+def test_invalid_arguments():
+    torch, dev = torch_cuda()
+    with pytest.raises(rg.RGError) as ei:
+        rg.RankGreville(0)
+    assert ei.value.code == rg.RG_EINVAL
+    with pytest.raises(rg.RGError):
+        rg.RankGreville(4, tol=float("nan"))
+    st = rg.RankGreville(4)
+    with pytest.raises(rg.RGError):
+        st.solution(None)
