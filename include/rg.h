@@ -194,6 +194,34 @@ rg_status rg_batch_reset(rg_batch* bt);
 /* rg_batch_free -- release (synchronises first). NULL is a no-op. */
 rg_status rg_batch_free(rg_batch* bt);
 
+/*
+ * rg_solve_noalloc -- solve one stream from scratch (Algorithm 1 over the n rows, as
+ * rg_init + rg_add_rows + rg_solution would) WITHOUT allocating any memory. The paper has
+ * no counterpart: this entry point exists for callers that cannot call cudaMalloc, for
+ * example a latency-critical loop that cannot accept cudaMalloc's implicit device
+ * synchronisation, or a host application whose device memory is owned entirely by its own
+ * allocator.
+ *   Gamma      device, n x m row-major FP64;  y  device, n FP64 targets;  n >= 0.
+ *   m, tol, flags, r_max: as rg_init.
+ *   X          device, m FP64: receives the minimum-norm least-squares solution.
+ *   rank_out   host, may be NULL. When given, the call synchronises the stream, stores the
+ *              rank and returns any device-side error (non-finite row, capacity); when
+ *              NULL the call is asynchronous and device-side errors are not reported.
+ *   cuda_stream  cudaStream_t for all work (NULL: legacy default stream).
+ * State and scratch live in one fixed file-scope device array of 8 MiB that every GPU
+ * loading the library holds until the process exits; a problem whose state and scratch do
+ * not fit (with r_max = m: m above 558 in FP64, above 608 in mixed mode; a smaller r_max
+ * raises the limit) is rejected with RG_EINVAL and a message.
+ * Every call shares that array and clears what must start at zero itself; calls that
+ * overlap on the GPU (different streams or host threads) race on it and must be
+ * serialised by the caller. The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.
+ */
+rg_status rg_solve_noalloc(const double* Gamma, const double* y, int64_t n, int64_t m,
+                           double tol, int flags, int64_t r_max, double* X, int64_t* rank_out,
+                           void* cuda_stream);
+
 /* Thread-local description of the last error returned on this thread ("" if none). */
 const char* rg_last_error(void);
 

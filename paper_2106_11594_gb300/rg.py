@@ -64,6 +64,7 @@ def lib(build: bool = True):
         "rg_batch_sync": [vp],
         "rg_batch_reset": [vp],
         "rg_batch_free": [vp],
+        "rg_solve_noalloc": [vp, vp, i64, i64, f64, i32, i64, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -99,6 +100,21 @@ def _need_cuda():
     import torch
     if not torch.cuda.is_available():
         raise RGError(RG_ECUDA, "rg", "no CUDA device: librg has no CPU fallback")
+
+
+def solve_noalloc(Gamma, y, X, tol: float = 1e-10, mode: int = RG_FP64,
+                  test: int = RG_TEST_REL, r_max: int = 0, stream=None, with_rank: bool = True):
+    """rg_solve_noalloc: one stream from scratch with no allocation inside the library.
+    Gamma (n, m), y (n,), X (m,) are float64 CUDA tensors. Returns the rank (synchronising)
+    or None when with_rank is False (asynchronous)."""
+    _need_cuda()
+    n = Gamma.shape[0]
+    m = Gamma.shape[1]
+    r = ctypes.c_int64(0)
+    _check(lib().rg_solve_noalloc(_ptr(Gamma), _ptr(y), n, m, float(tol), int(mode) | int(test),
+                                  int(r_max), _ptr(X), ctypes.byref(r) if with_rank else None,
+                                  _stream(stream)), "rg_solve_noalloc")
+    return int(r.value) if with_rank else None
 
 
 class RankGreville:
