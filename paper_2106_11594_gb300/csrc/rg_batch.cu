@@ -52,14 +52,19 @@ __host__ __device__ inline size_t inst_layout(int m, int ld, int rmax, int mixed
   char* C = take((size_t)rmax * ld * 8);
   char* Ct = mixed ? nullptr : take((size_t)rmax * ld * 8);
   char* Qf = mixed ? take((size_t)rmax * ld * 4) : nullptr;
-  char* Pinv = take((size_t)rmax * rmax * 8);
+  char* P = take((size_t)rmax * rmax * 8);
+  char* wb = take((size_t)rmax * 8);
+  char* u = take((size_t)rmax * 8);
   char* w = take((size_t)rmax * 8);
   char* basis = take((size_t)rmax * 8);
   if (S) {
     S->C = (double*)C;
     S->Ct = (double*)Ct;
     S->Qf = (float*)Qf;
-    S->Pinv = (double*)Pinv;
+    S->Pinv = nullptr;
+    S->P = (double*)P;
+    S->wb = (double*)wb;
+    S->u = (double*)u;
     S->w = (double*)w;
     S->basis_rows = (long long*)basis;
   }
@@ -87,13 +92,16 @@ __host__ __device__ inline size_t scratch_layout(int kb, int ldm, int rmm, int n
   char* Gind = take((size_t)SLOW_MAX * rmm * 8);
   char* alpha = take((size_t)SLOW_MAX * 8);
   char* jind = take((size_t)SLOW_MAX * 4);
-  char* seg = take((size_t)3 * (SLOW_MAX + 2) * 4);
-  char* Zt = take((size_t)SB * rmm * 8);
-  char* M = take((size_t)SB * SB * 8);
-  char* Wt = take((size_t)SB * rmm * 8);
-  char* D = take((size_t)SB * 8);
-  char* aw = take((size_t)SB * 8);
+  char* Dall = take((size_t)kb * 8);
+  char* Pp = take((size_t)rmm * rmm * 8);  // one chunk: a CTA team gains nothing from more
+  char* up = take((size_t)NCH_MAX * rmm * 8);
+  char* Lw = take((size_t)rmm * rmm * 8);
   if (S) {
+    S->Dall = (double*)Dall;
+    S->Pp = (double*)Pp;
+    S->pp_cap = (size_t)rmm * rmm;
+    S->up = (double*)up;
+    S->Lw = (double*)Lw;
     S->G = (double*)G;
     S->spart = (double*)sp;
     S->tpart = (double*)tp;
@@ -105,12 +113,6 @@ __host__ __device__ inline size_t scratch_layout(int kb, int ldm, int rmm, int n
     S->Gind = (double*)Gind;
     S->alpha = (double*)alpha;
     S->jind = (int*)jind;
-    S->seg = (int*)seg;
-    S->Zt = (double*)Zt;
-    S->M = (double*)M;
-    S->Wt = (double*)Wt;
-    S->D = (double*)D;
-    S->aw = (double*)aw;
   }
   return off;
 }
@@ -209,13 +211,23 @@ __global__ void order_kernel(BatchDev D, const int64_t* __restrict__ roff) {
   for (int b = threadIdx.x; b < B; b += blockDim.x) D.order[b] = (int)(keys[b] & 0xFFFFFull);
 }
 
-__global__ void batch_solution_kernel(BatchDev D, double* X, const int64_t* xoff, int64_t* ranks) {
+// One CTA per instance (strided): w = w_b + P^-1 u in the CTA's scratch slab, then X.
+__global__ void __launch_bounds__(NT, 2) batch_solution_kernel(BatchDev D, double* X, const int64_t* xoff,
+                                                              int64_t* ranks) {
+  StreamDev S{};
+  scratch_layout(D.kb_max, D.ld_max, D.r_max_max, D.nmc_max,
+                 D.scratch + (size_t)blockIdx.x * D.scratch_stride, &S);
   for (int b = blockIdx.x; b < D.B; b += gridDim.x) {
     const int m = D.m[b];
-    StreamDev S{};
     const int ld = (m + 3) / 4 * 4;
+    S.m = m;
+    S.ld = ld;
+    S.r_max = D.r_max[b];
+    S.ctrl = D.ctrl + (size_t)b * CTRL_N;
     inst_layout(m, ld, D.r_max[b], D.mixed, D.state + D.soff[b], &S);
     const int r = D.ctrl[(size_t)b * CTRL_N + CTRL_R];
+    __syncthreads();
+    form_w(S, r);
     const double* Bm = D.mixed ? S.C : S.Ct;
     const long long x0 = xoff ? xoff[b] : D.xoff_def[b];
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
@@ -405,8 +417,7 @@ rg_status rg_batch_add_rows(rg_batch* bt, const double* Gamma_packed, const int6
 rg_status rg_batch_solution(rg_batch* bt, double* X_packed, const int64_t* x_offsets, int64_t* ranks_out) {
   if (!valid_batch(bt)) return fail(RG_EINVAL, "rg_batch_solution: invalid batch");
   if (!X_packed) return fail(RG_EINVAL, "rg_batch_solution: X is NULL");
-  const int grid = std::min(bt->D.B, 4096);
-  batch_solution_kernel<<<grid, 256, 0, bt->stream>>>(bt->D, X_packed, x_offsets, ranks_out);
+  batch_solution_kernel<<<bt->grid, NT, 0, bt->stream>>>(bt->D, X_packed, x_offsets, ranks_out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "rg_batch_solution: launch");
   return RG_OK;

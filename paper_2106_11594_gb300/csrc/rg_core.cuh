@@ -4,12 +4,29 @@
 // A Team provides id() / size() (this worker and the number of workers; work items are
 // strided over workers) and sync() (a barrier over the team that returns false if a
 // bounded wait ran out).
+//
+// State (Section 2.1): the basis C (or Q), its dual Ct, and the small matrices in
+// information form: P = B^T B (so P^-1 of Algorithm 1 is its inverse) and the solution
+// coordinates w = w_b + P^-1 u with X = Ct^T w (from A^+ = Ct^T P^-1 B^T). A dependent row
+// (Theorem 6, dependent case; Theorem 5) adds gamma gamma^T to P and gamma (y - gamma^T w_b)
+// to u: P^-1 <- P^-1 - zeta zeta^T / (1 + gamma^T zeta) is exactly the inverse of
+// P <- P + gamma gamma^T (Sherman-Morrison, Eq. label_eq_sherman_morrison), and
+// w_new = w_b + P_new^-1 (u + gamma (y - gamma^T w_b)) holds for any base w_b. An
+// independent row extends the state (Theorem 6, independent case): general variant
+// P <- diag(P, 1), w_b <- [w_b; y], u <- [u; 0]; orthonormal variant (Section 2.2)
+// P <- diag(P, 0) + g g^T with g = [gamma; 1/alpha], w_b <- [w_b; 0], u <- [u; 0] +
+// g (y - gamma^T w_b). P^-1 and w are formed (Cholesky of P) only when X or an export is
+// requested, so no sequential small solve sits on the row path.
+//
+// Data written by one worker and read by another within a launch is always read with
+// __ldcg (L2), never through the non-coherent L1.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "rg_internal.cuh"
 
@@ -38,285 +55,30 @@ struct CtaTeam {
   }
 };
 
-
-// ---------------------------------------------------------------------------------------
-// Phase 1: gamma. Warp item = (group of JW block rows, one basis row i). The basis row is
-// Ct_i (general) or Q_i (orthonormal); F32 projects with the FP32 copy of Q.
-// ---------------------------------------------------------------------------------------
-template <class Team, bool F32>
-__device__ void phase_gamma(const Team& T, const StreamDev& S, const double* __restrict__ gam, int row_lo,
-                            int row_hi, int r, const double* __restrict__ basis64) {
-  const int nrows = row_hi - row_lo;
-  if (nrows <= 0 || r <= 0) return;
-  const int m = S.m, ld = S.ld;
-  const int ngroups = (nrows + JW - 1) / JW;
-  const long long nitems = (long long)ngroups * r;
-  const int lane = threadIdx.x & 31;
-  const long long wstride = (long long)T.size() * NWARP;
-  for (long long it = (long long)T.id() * NWARP + (threadIdx.x >> 5); it < nitems;
-       it += wstride) {
-    const int grp = (int)(it / r);
-    const int i = (int)(it - (long long)grp * r);
-    const int jbase = row_lo + grp * JW;
-    const int nj = min(JW, row_hi - jbase);
-    if (F32) {
-      float acc[JW];
-#pragma unroll
-      for (int a = 0; a < JW; ++a) acc[a] = 0.f;
-      const float* q = S.Qf + (size_t)i * ld;
-      for (int c = lane; c < m; c += 32) {
-        const float qv = __ldcg(q + c);
-#pragma unroll
-        for (int a = 0; a < JW; ++a)
-          if (a < nj) acc[a] = fmaf(qv, (float)__ldg(gam + (size_t)(jbase + a) * m + c), acc[a]);
-      }
-#pragma unroll
-      for (int a = 0; a < JW; ++a) {
-        const float v = warp_sumf(acc[a]);
-        if (lane == 0 && a < nj) S.G[(size_t)(jbase + a) * S.r_max + i] = (double)v;
-      }
-    } else {
-      double acc[JW];
-#pragma unroll
-      for (int a = 0; a < JW; ++a) acc[a] = 0.0;
-      const double* q = basis64 + (size_t)i * ld;
-      for (int c = lane; c < m; c += 32) {
-        const double qv = __ldcg(q + c);
-#pragma unroll
-        for (int a = 0; a < JW; ++a)
-          if (a < nj) acc[a] = fma(qv, __ldg(gam + (size_t)(jbase + a) * m + c), acc[a]);
-      }
-#pragma unroll
-      for (int a = 0; a < JW; ++a) {
-        const double v = warp_sum(acc[a]);
-        if (lane == 0 && a < nj) S.G[(size_t)(jbase + a) * S.r_max + i] = v;
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------------------
-// Phase 2: rejection. CTA item = (RJ block rows) x (MC columns); one thread per
-// (row, column). Writes per-chunk partial sums of ||Gamma_r||^2 and ||Gamma||^2 and, when
-// Rout != null, the FP64 rejection vectors (row j at Rout[(j - row_lo) * ld]).
-// ---------------------------------------------------------------------------------------
-template <class Team, bool F32>
-__device__ void phase_reject(const Team& T, const StreamDev& S, const double* __restrict__ gam, int row_lo,
-                             int row_hi, int r, const double* __restrict__ back64,
-                             double* __restrict__ Rout) {
-  const int nrows = row_hi - row_lo;
-  if (nrows <= 0) return;
-  const int m = S.m, ld = S.ld, nmc = S.nmc;
-  const int ngroups = (nrows + RJ - 1) / RJ;
-  const long long nitems = (long long)ngroups * nmc;
-  __shared__ double red_s[NWARP], red_t[NWARP];
-  const int jj = threadIdx.x / MC;
-  const int cc = threadIdx.x % MC;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (long long it = T.id(); it < nitems; it += T.size()) {
-    const int grp = (int)(it / nmc);
-    const int mc = (int)(it - (long long)grp * nmc);
-    const int j = row_lo + grp * RJ + jj;
-    const int c = mc * MC + cc;
-    double sv = 0.0, tv = 0.0;
-    if (j < row_hi && c < m) {
-      const double gv = __ldg(gam + (size_t)j * m + c);
-      const double* gj = S.G + (size_t)j * S.r_max;
-      if (F32) {
-        float acc = (float)gv;
-        for (int i = 0; i < r; ++i)
-          acc = fmaf(-__ldcg(S.Qf + (size_t)i * ld + c), (float)__ldcg(gj + i), acc);
-        sv = (double)acc * (double)acc;
-      } else {
-        double acc = gv;
-        for (int i = 0; i < r; ++i) acc = fma(-__ldcg(back64 + (size_t)i * ld + c), __ldcg(gj + i), acc);
-        sv = acc * acc;
-        if (Rout) Rout[(size_t)(j - row_lo) * ld + c] = acc;
-      }
-      tv = gv * gv;
-    }
-    sv = warp_sum(sv);
-    tv = warp_sum(tv);
-    __syncthreads();
-    if (lane == 0) {
-      red_s[warp] = sv;
-      red_t[warp] = tv;
-    }
-    __syncthreads();
-    // MC = 64 columns per row = 2 warps per row
-    if (threadIdx.x < RJ) {
-      const int jr = row_lo + grp * RJ + threadIdx.x;
-      if (jr < row_hi) {
-        S.spart[(size_t)jr * nmc + mc] = red_s[2 * threadIdx.x] + red_s[2 * threadIdx.x + 1];
-        S.tpart[(size_t)jr * nmc + mc] = red_t[2 * threadIdx.x] + red_t[2 * threadIdx.x + 1];
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------------------
-// Phase 3 (CTA 0): reduce the partial norms, decide every row, find the first row that
-// needs the sequential section (independent, FP32 candidate, or non-finite).
-// ---------------------------------------------------------------------------------------
-template <bool MIXED>
-__device__ void phase_decide(const StreamDev& S, const CallArgs& A, long long j0, int b, int r) {
-  __shared__ int q0;
-  if (threadIdx.x == 0) q0 = b;
-  __syncthreads();
-  const int nmc = S.nmc;
-  double tc = S.tau_lo;
-  if (MIXED && S.test_mode == 0 && S.tol > 0.0) tc = fmax(tc, 0.5 * S.tol);
-  for (int j = threadIdx.x; j < b; j += NT) {
-    double s = 0.0, t = 0.0;
-    for (int c = 0; c < nmc; ++c) {
-      s += __ldcg(S.spart + (size_t)j * nmc + c);
-      t += __ldcg(S.tpart + (size_t)j * nmc + c);
-    }
-    S.s[j] = s;
-    S.t[j] = t;
-    const double yv = __ldg(A.y + j0 + j);
-    bool special = !isfinite(t) || !isfinite(yv);
-    if (!special) {
-      if (MIXED) special = s > tc * tc * t;
-      else special = is_independent(s, t, r, S.m, S.tol, S.test_mode);
-    }
-    if (special) atomicMin(&q0, j);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) S.ctrl[CTRL_Q0] = q0;
-}
-
-// ---------------------------------------------------------------------------------------
-// Blocked Sherman-Morrison (Woodbury) update of P^-1 and w for dependent block rows
-// [a, a + len) whose gammas (length r) are in S.G. Every CTA calls it (grid phases).
-// Returns false if a grid barrier timed out.
-// ---------------------------------------------------------------------------------------
+// Work-item numbering that deals consecutive items to different workers first, so that a
+// phase with few items still spreads over every SM (FP64 throughput is per SM).
 template <class Team>
-__device__ bool woodbury(const Team& T, const StreamDev& S, const CallArgs& A, long long j0, int a, int len,
-                         int r) {
-  const int lane = threadIdx.x & 31;
-  const long long gw = (long long)T.id() * NWARP + (threadIdx.x >> 5);
-  const long long wstride = (long long)T.size() * NWARP;
-  const long long gt = (long long)T.id() * NT + threadIdx.x;
-  const long long tstride = (long long)T.size() * NT;
-  const int rm = S.r_max;
-  __shared__ double Ls[SB * SB];
-  __shared__ double zs[SB];
-  for (int s0 = a; s0 < a + len; s0 += SB) {
-    const int q = min(SB, a + len - s0);
-    if (r == 0) continue;  // zero rows with an empty basis: K = 0, nothing changes
-    // W1: zeta_j = P^-1 gamma_j (Zt row j), D_j = y_j - gamma_j^T w
-    {
-      const long long nitems = (long long)r * q + q;
-      for (long long it = gw; it < nitems; it += wstride) {
-        double acc = 0.0;
-        if (it < (long long)r * q) {
-          const int jj = (int)(it / r), i = (int)(it - (long long)jj * r);
-          const double* g = S.G + (size_t)(s0 + jj) * rm;
-          const double* p = S.Pinv + (size_t)i * rm;
-          for (int l = lane; l < r; l += 32) acc = fma(__ldcg(p + l), __ldcg(g + l), acc);
-          acc = warp_sum(acc);
-          if (lane == 0) S.Zt[(size_t)jj * rm + i] = acc;
-        } else {
-          const int jj = (int)(it - (long long)r * q);
-          const double* g = S.G + (size_t)(s0 + jj) * rm;
-          for (int l = lane; l < r; l += 32) acc = fma(__ldcg(g + l), __ldcg(S.w + l), acc);
-          acc = warp_sum(acc);
-          if (lane == 0) S.D[jj] = __ldg(A.y + j0 + s0 + jj) - acc;
-        }
-      }
-    }
-    if (!T.sync()) return false;
-    // W2: M = I + G^T Z (lower triangle)
-    {
-      const long long nitems = (long long)q * q;
-      for (long long it = gw; it < nitems; it += wstride) {
-        const int p = (int)(it / q), p2 = (int)(it - (long long)p * q);
-        if (p2 > p) continue;
-        const double* g = S.G + (size_t)(s0 + p) * rm;
-        const double* z = S.Zt + (size_t)p2 * rm;
-        double acc = 0.0;
-        for (int l = lane; l < r; l += 32) acc = fma(__ldcg(g + l), __ldcg(z + l), acc);
-        acc = warp_sum(acc);
-        if (lane == 0) S.M[p * SB + p2] = acc + (p == p2 ? 1.0 : 0.0);
-      }
-    }
-    if (!T.sync()) return false;
-    // W3a (CTA 0): Cholesky M = L L^T and a = M^-1 D
-    if (T.id() == 0) {
-      for (int e = threadIdx.x; e < q * q; e += NT) {
-        const int p = e / q, p2 = e - p * q;
-        Ls[p * SB + p2] = (p2 <= p) ? __ldcg(S.M + p * SB + p2) : 0.0;
-      }
-      if (threadIdx.x < q) zs[threadIdx.x] = __ldcg(S.D + threadIdx.x);
-      __syncthreads();
-      for (int kk = 0; kk < q; ++kk) {
-        if (threadIdx.x == 0) {
-          const double d = Ls[kk * SB + kk];
-          if (!(d > 0.0) || !isfinite(d)) atomicOr(S.ctrl + CTRL_STATUS, ST_NONFINITE);
-          Ls[kk * SB + kk] = sqrt(fmax(d, 1e-300));
-        }
-        __syncthreads();
-        const double lkk = Ls[kk * SB + kk];
-        for (int p = kk + 1 + threadIdx.x; p < q; p += NT) Ls[p * SB + kk] /= lkk;
-        __syncthreads();
-        const int rem = q - kk - 1;
-        for (int e = threadIdx.x; e < rem * rem; e += NT) {
-          const int p = kk + 1 + e / rem, p2 = kk + 1 + e % rem;
-          if (p2 <= p) Ls[p * SB + p2] -= Ls[p * SB + kk] * Ls[p2 * SB + kk];
-        }
-        __syncthreads();
-      }
-      if (threadIdx.x == 0) {
-        for (int p = 0; p < q; ++p) {  // forward: L z = D
-          double v = zs[p];
-          for (int p2 = 0; p2 < p; ++p2) v -= Ls[p * SB + p2] * zs[p2];
-          zs[p] = v / Ls[p * SB + p];
-        }
-        for (int p = q - 1; p >= 0; --p) {  // backward: L^T a = z
-          double v = zs[p];
-          for (int p2 = p + 1; p2 < q; ++p2) v -= Ls[p2 * SB + p] * zs[p2];
-          zs[p] = v / Ls[p * SB + p];
-        }
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < q * q; e += NT) {
-        const int p = e / q, p2 = e - p * q;
-        S.M[p * SB + p2] = Ls[p * SB + p2];
-      }
-      if (threadIdx.x < q) S.aw[threadIdx.x] = zs[threadIdx.x];
-    }
-    if (!T.sync()) return false;
-    // W3b: Wt = L^-1 Z^T column by column; w += Z a
-    for (long long i = gt; i < r; i += tstride) {
-      double wi = __ldcg(S.w + i);
-      for (int p = 0; p < q; ++p) {
-        const double zpi = __ldcg(S.Zt + (size_t)p * rm + i);
-        wi = fma(zpi, __ldcg(S.aw + p), wi);
-        double v = zpi;
-        for (int p2 = 0; p2 < p; ++p2) v -= __ldcg(S.M + p * SB + p2) * __ldcg(S.Wt + (size_t)p2 * rm + i);
-        S.Wt[(size_t)p * rm + i] = v / __ldcg(S.M + p * SB + p);
-      }
-      S.w[i] = wi;
-    }
-    if (!T.sync()) return false;
-    // W4: P^-1 <- P^-1 - Wt^T Wt
-    {
-      const long long nitems = (long long)r * r;
-      for (long long it = gt; it < nitems; it += tstride) {
-        const int i = (int)(it / r), l = (int)(it - (long long)i * r);
-        double acc = 0.0;
-        for (int p = 0; p < q; ++p)
-          acc = fma(__ldcg(S.Wt + (size_t)p * rm + i), __ldcg(S.Wt + (size_t)p * rm + l), acc);
-        S.Pinv[(size_t)i * rm + l] = __ldcg(S.Pinv + (size_t)i * rm + l) - acc;
-      }
-    }
-    if (!T.sync()) return false;
-  }
-  return true;
+__device__ __forceinline__ long long rr_warp(const Team& T) {
+  return (long long)(threadIdx.x >> 5) * T.size() + T.id();
+}
+template <class Team>
+__device__ __forceinline__ long long rr_thread(const Team& T) {
+  return (long long)threadIdx.x * T.size() + T.id();
 }
 
-// Block-wide sum (all threads get the result).
+// 1/sqrt(d) for d > 0: single-precision seed refined by two Newton-Raphson steps
+// y <- y (3 - d y^2) / 2 (quadratic convergence: ~2^-22 -> ~2^-44 -> rounding level).
+// Falls back to 1/sqrt outside the single-precision range.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+  const double h = 0.5 * d;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+
+// CTA-wide sum; every thread gets the result.
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double red[NWARP];
   __shared__ double tot;
@@ -333,20 +95,509 @@ __device__ __forceinline__ double block_sum(double v) {
   return tot;
 }
 
-// ---------------------------------------------------------------------------------------
-// Sequential section scan (CTA 0): rows [q0, bend) with FP64 G and R (R row j at
+// One shared-memory pool per CTA for the larger working arrays of the phases below; the
+// phases that use it are separated by barriers, so they never overlap.
+constexpr int POOL_DOUBLES = 4352;  // 34 KiB: a 64 x 64 tile plus 4 rows of 64
+static_assert(32 * 33 + GRAM_RMAX <= POOL_DOUBLES, "solve staging must fit the pool");
+static_assert(3 * 32 * 33 <= POOL_DOUBLES, "Cholesky tiles must fit the pool");
+static_assert(64 * MC + RJ * 64 <= POOL_DOUBLES, "rejection tiles must fit the pool");
+__device__ __forceinline__ double* smem_pool() {
+  __shared__ __align__(16) double pool[POOL_DOUBLES];
+  return pool;
+}
+
+// Butterfly all-reduce of 32 values across the 32 lanes of a warp: on entry every lane
+// holds v[0..31]; on exit lane l holds in v[0] the sum over lanes of v[l]. Each of the
+// five stages exchanges half of the remaining values (16 + 8 + 4 + 2 + 1 shuffles), and
+// the adds within a stage are independent, so the FP64 add latency overlaps.
+__device__ __forceinline__ void warp_transpose_sum32(double (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < off; ++k) {
+      const double send = upper ? v[k] : v[k + off];
+      const double keep = upper ? v[k + off] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+}
+
+// Generalisation to N = 2^k <= 32 values per lane (type V): the first k stages split the
+// values by lane bits 4, 3, ..., the remaining 5 - k stages are plain butterflies. On
+// exit lane l holds in v[0] the total for value index (l >> (5 - k)) mod N, bit-reversed
+// order not needed: index = sum of lane bits 4..(5-k) weighted N/2, N/4, ..., 1.
+template <typename V, int N>
+__device__ __forceinline__ V warp_transpose_sum(V (&v)[N]) {
+  const int lane = threadIdx.x & 31;
+  int cur = N;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    if (cur > 1) {
+      const bool upper = (lane & off) != 0;
+      const int half = cur >> 1;
+#pragma unroll
+      for (int k = 0; k < N / 2; ++k) {
+        if (k < half) {
+          const V send = upper ? v[k] : v[k + half];
+          const V keep = upper ? v[k + half] : v[k];
+          v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+      }
+      cur = half;
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+    }
+  }
+  return v[0];
+}
+// Value index held by this lane after warp_transpose_sum<V, N>.
+template <int N>
+__device__ __forceinline__ int transpose_sum_index() {
+  const int lane = threadIdx.x & 31;
+  int idx = 0, w = N >> 1;
+#pragma unroll
+  for (int off = 16; off >= 1 && w >= 1; off >>= 1, w >>= 1)
+    if (lane & off) idx += w;
+  return idx;
+}
+
+// =======================================================================================
+// Projection of a block of rows against the block-start basis
+// =======================================================================================
+
+// gamma_j = Ct Gamma_j (general) or Q Gamma_j (orthonormal) for rows [row_lo, row_hi).
+// Warp item = (NJ rows) x (NI basis rows), dealt round robin over the workers; the lanes
+// stride over the m columns and the NJ x NI partial sums are combined by one butterfly
+// transpose-reduction. FP64: NJ = 8, NI = 1 (FP64 adds are scarce on this part, so the
+// reduction is kept to ~3% of the FMAs). F32 (FP32 copy of Q): NJ = 4, NI = 8, FP32
+// accumulation, each FP64 input element converted once per item.
+template <class Team, bool F32>
+__device__ void phase_gamma(const Team& T, const StreamDev& S, const double* __restrict__ gam,
+                            int row_lo, int row_hi, int r, const double* __restrict__ basis64) {
+  constexpr int NJ = F32 ? 4 : 8, NI = F32 ? 8 : 1, N = NJ * NI;
+  using V = typename std::conditional<F32, float, double>::type;
+  const int nrows = row_hi - row_lo;
+  if (nrows <= 0 || r <= 0) return;
+  const int m = S.m, ld = S.ld, rm = S.r_max;
+  const int nj = (nrows + NJ - 1) / NJ, ni = (r + NI - 1) / NI;
+  const long long nitems = (long long)nj * ni;
+  const long long wstride = (long long)T.size() * NWARP;
+  const int lane = threadIdx.x & 31;
+  for (long long it = rr_warp(T); it < nitems; it += wstride) {
+    const int gj = (int)(it / ni), gi = (int)(it - (long long)gj * ni);
+    const int j0 = row_lo + gj * NJ, i0 = gi * NI;
+    V acc[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) acc[q] = V(0);
+#pragma unroll 8
+    for (int c = lane; c < m; c += 32) {
+      V gv[NJ], bv[NI];
+#pragma unroll
+      for (int a = 0; a < NJ; ++a) gv[a] = (j0 + a < row_hi) ? (V)__ldg(gam + (size_t)(j0 + a) * m + c) : V(0);
+#pragma unroll
+      for (int bb = 0; bb < NI; ++bb) {
+        if (F32) bv[bb] = (i0 + bb < r) ? (V)__ldcg(S.Qf + (size_t)(i0 + bb) * ld + c) : V(0);
+        else bv[bb] = (i0 + bb < r) ? (V)__ldcg(basis64 + (size_t)(i0 + bb) * ld + c) : V(0);
+      }
+#pragma unroll
+      for (int a = 0; a < NJ; ++a)
+#pragma unroll
+        for (int bb = 0; bb < NI; ++bb) acc[a * NI + bb] = fma(bv[bb], gv[a], acc[a * NI + bb]);
+    }
+    const V tot = warp_transpose_sum<V, N>(acc);
+    const int q = transpose_sum_index<N>();
+    // the lanes holding index q are those with equal high bits; the lowest one writes
+    const int low_bits = 32 / N;  // lanes sharing an index: low (5 - log2 N) bits free
+    if ((lane & (low_bits - 1)) == 0) {
+      const int a = q / NI, bb = q - a * NI;
+      if (j0 + a < row_hi && i0 + bb < r) S.G[(size_t)(j0 + a) * rm + i0 + bb] = (double)tot;
+    }
+  }
+}
+
+// Gamma_r = Gamma_j - B^T gamma_j with B = C (general) or Q (orthonormal). CTA item =
+// (RJ rows) x (MC columns), one thread per (row, column). The basis tile (64 ranks x MC
+// columns) and the RJ gamma rows are staged in shared memory per chunk of 64 ranks, so
+// each chunk costs one round of coalesced loads; the sum runs in four chains. Writes
+// per-chunk partial sums of ||Gamma_r||^2 and ||Gamma||^2 and, when Rout != null, the
+// FP64 rejections (row j at Rout[(j - row_lo) * ld]).
+template <class Team, bool F32>
+__device__ void phase_reject(const Team& T, const StreamDev& S, const double* __restrict__ gam,
+                             int row_lo, int row_hi, int r, const double* __restrict__ back64,
+                             double* __restrict__ Rout) {
+  const int nrows = row_hi - row_lo;
+  if (nrows <= 0) return;
+  constexpr int RC = 64;  // ranks per staged chunk
+  const int m = S.m, ld = S.ld, nmc = S.nmc, rm = S.r_max;
+  const int ngroups = (nrows + RJ - 1) / RJ;
+  const long long nitems = (long long)ngroups * nmc;
+  __shared__ double red_s[NWARP], red_t[NWARP];
+  double* Bt = smem_pool();     // RC x MC basis tile (FP64 or FP32 values)
+  float* Btf = reinterpret_cast<float*>(Bt);
+  double* Gs = Bt + RC * MC;    // RJ x RC gamma slice
+  const int jj = threadIdx.x / MC;
+  const int cc = threadIdx.x % MC;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (long long it = T.id(); it < nitems; it += T.size()) {
+    const int grp = (int)(it / nmc);
+    const int mc = (int)(it - (long long)grp * nmc);
+    const int j = row_lo + grp * RJ + jj;
+    const int c = mc * MC + cc;
+    const bool valid = (j < row_hi && c < m);
+    const double gv = valid ? __ldg(gam + (size_t)j * m + c) : 0.0;
+    double a0 = gv, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    float f0 = (float)gv, f1 = 0.f;
+    for (int i0 = 0; i0 < r; i0 += RC) {
+      const int rc = min(RC, r - i0);
+      __syncthreads();
+#pragma unroll 16
+      for (int e = threadIdx.x; e < rc * MC; e += NT) {
+        const int ii = e / MC, c2 = mc * MC + (e - ii * MC);
+        if (F32) Btf[e] = (c2 < m) ? __ldcg(S.Qf + (size_t)(i0 + ii) * ld + c2) : 0.f;
+        else Bt[e] = (c2 < m) ? __ldcg(back64 + (size_t)(i0 + ii) * ld + c2) : 0.0;
+      }
+      float* Gsf = reinterpret_cast<float*>(Gs);
+      for (int e = threadIdx.x; e < RJ * rc; e += NT) {
+        const int a = e / rc, ii = e - a * rc;
+        const int ja = row_lo + grp * RJ + a;
+        const double gvv = (ja < row_hi) ? __ldcg(S.G + (size_t)ja * rm + i0 + ii) : 0.0;
+        if (F32) Gsf[a * RC + ii] = (float)gvv;
+        else Gs[a * RC + ii] = gvv;
+      }
+      __syncthreads();
+      const double* g = Gs + jj * RC;
+      if (F32) {
+        const float* gf = Gsf + jj * RC;
+        int ii = 0;
+        for (; ii + 1 < rc; ii += 2) {
+          f0 = fmaf(-Btf[ii * MC + cc], gf[ii], f0);
+          f1 = fmaf(-Btf[(ii + 1) * MC + cc], gf[ii + 1], f1);
+        }
+        if (ii < rc) f0 = fmaf(-Btf[ii * MC + cc], gf[ii], f0);
+      } else {
+        int ii = 0;
+        for (; ii + 3 < rc; ii += 4) {
+          a0 = fma(-Bt[ii * MC + cc], g[ii], a0);
+          a1 = fma(-Bt[(ii + 1) * MC + cc], g[ii + 1], a1);
+          a2 = fma(-Bt[(ii + 2) * MC + cc], g[ii + 2], a2);
+          a3 = fma(-Bt[(ii + 3) * MC + cc], g[ii + 3], a3);
+        }
+        for (; ii < rc; ++ii) a0 = fma(-Bt[ii * MC + cc], g[ii], a0);
+      }
+    }
+    double sv = 0.0, tv = 0.0;
+    if (valid) {
+      if (F32) {
+        const float acc = f0 + f1;
+        sv = (double)acc * (double)acc;
+      } else {
+        const double acc = (a0 + a1) + (a2 + a3);
+        sv = acc * acc;
+        if (Rout) Rout[(size_t)(j - row_lo) * ld + c] = acc;
+      }
+      tv = gv * gv;
+    }
+    sv = warp_sum(sv);
+    tv = warp_sum(tv);
+    __syncthreads();
+    if (lane == 0) {
+      red_s[warp] = sv;
+      red_t[warp] = tv;
+    }
+    __syncthreads();
+    if (threadIdx.x < RJ) {  // MC = 64 columns per row = 2 warps per row
+      const int jr = row_lo + grp * RJ + threadIdx.x;
+      if (jr < row_hi) {
+        S.spart[(size_t)jr * nmc + mc] = red_s[2 * threadIdx.x] + red_s[2 * threadIdx.x + 1];
+        S.tpart[(size_t)jr * nmc + mc] = red_t[2 * threadIdx.x] + red_t[2 * threadIdx.x + 1];
+      }
+    }
+  }
+}
+
+// A-priori errors D_j = y_j - gamma_j^T w_b of rows [0, b) (Theorems 4/5 with the
+// solution in base coordinates). Warp items, one row each.
+template <class Team>
+__device__ void phase_dall(const Team& T, const StreamDev& S, const CallArgs& A, long long j0, int b,
+                           int r) {
+  const int lane = threadIdx.x & 31;
+  const long long wstride = (long long)T.size() * NWARP;
+  for (long long j = rr_warp(T); j < b; j += wstride) {
+    const double* g = S.G + (size_t)j * S.r_max;
+    double acc = 0.0;
+    for (int l = lane; l < r; l += 32) acc = fma(__ldcg(g + l), __ldcg(S.wb + l), acc);
+    acc = warp_sum(acc);
+    if (lane == 0) S.Dall[j] = __ldg(A.y + j0 + j) - acc;
+  }
+}
+
+// Reduce the partial norms of rows [0, b), decide every row and return the first row that
+// needs the sequential section (independent, FP32 candidate, or non-finite). Every CTA that
+// calls it gets the same answer (same data, same summation order); with `publish` the CTA
+// also stores s, t and the answer for the later phases.
+template <bool MIXED>
+__device__ int decide_rows(const StreamDev& S, const CallArgs& A, long long j0, int b, int r,
+                           bool publish) {
+  __shared__ int q0;
+  if (threadIdx.x == 0) q0 = b;
+  __syncthreads();
+  const int nmc = S.nmc;
+  double tc = S.tau_lo;
+  if (MIXED && S.test_mode == 0 && S.tol > 0.0) tc = fmax(tc, 0.5 * S.tol);
+  // a warp sums the chunk partials of rows warp, warp + NWARP, ...; all loads of up to
+  // four rows are issued before the reductions
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int jb = 0; jb < b; jb += 4 * NWARP) {
+    double s4[4], t4[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = jb + q * NWARP + warp;
+      s4[q] = 0.0;
+      t4[q] = 0.0;
+      if (j < b)
+        for (int c = lane; c < nmc; c += 32) {
+          s4[q] += __ldcg(S.spart + (size_t)j * nmc + c);
+          t4[q] += __ldcg(S.tpart + (size_t)j * nmc + c);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = jb + q * NWARP + warp;
+      const double s = warp_sum(s4[q]);
+      const double t = warp_sum(t4[q]);
+      if (lane == 0 && j < b) {
+        if (publish) {
+          S.s[j] = s;
+          S.t[j] = t;
+        }
+        const double yv = __ldg(A.y + j0 + j);
+        bool special = !isfinite(t) || !isfinite(yv);
+        if (!special) {
+          if (MIXED) special = s > tc * tc * t;
+          else special = is_independent(s, t, r, S.m, S.tol, S.test_mode);
+        }
+        if (special) atomicMin(&q0, j);
+      }
+    }
+  }
+  __syncthreads();
+  const int res = q0;
+  if (publish && threadIdx.x == 0) S.ctrl[CTRL_Q0] = res;
+  __syncthreads();
+  return res;
+}
+
+// Team-parallel form for large blocks: every warp decides rows (dealt round robin) and
+// lowers CTRL_Q0 with atomicMin; CTRL_Q0 must hold b beforehand (set in an earlier phase).
+// Stores s and t of every row.
+template <class Team, bool MIXED>
+__device__ void decide_rows_team(const Team& T, const StreamDev& S, const CallArgs& A, long long j0,
+                                 int b, int r) {
+  const int nmc = S.nmc;
+  double tc = S.tau_lo;
+  if (MIXED && S.test_mode == 0 && S.tol > 0.0) tc = fmax(tc, 0.5 * S.tol);
+  const int lane = threadIdx.x & 31;
+  const long long wstride = (long long)T.size() * NWARP;
+  for (long long j = rr_warp(T); j < b; j += wstride) {
+    double s = 0.0, t = 0.0;
+    for (int c = lane; c < nmc; c += 32) {
+      s += __ldcg(S.spart + (size_t)j * nmc + c);
+      t += __ldcg(S.tpart + (size_t)j * nmc + c);
+    }
+    s = warp_sum(s);
+    t = warp_sum(t);
+    if (lane == 0) {
+      S.s[j] = s;
+      S.t[j] = t;
+      const double yv = __ldg(A.y + j0 + j);
+      bool special = !isfinite(t) || !isfinite(yv);
+      if (!special) {
+        if (MIXED) special = s > tc * tc * t;
+        else special = is_independent(s, t, r, S.m, S.tol, S.test_mode);
+      }
+      if (special) atomicMin(S.ctrl + CTRL_Q0, (int)j);
+    }
+  }
+}
+
+// =======================================================================================
+// Dependent rows: P += gamma gamma^T, u += gamma D for rows of a run whose D are in S.Dall.
+// =======================================================================================
+
+// Short runs: one thread per entry of P (and of u), dealt round robin over the workers,
+// up to EMAX entries per thread per pass; the gamma rows of the run (and their D) are
+// staged in shared memory in row chunks. Ranks whose gamma rows do not fit the pool read
+// G from L2 directly.
+template <class Team>
+__device__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int r) {
+  const int rm = S.r_max;
+  const long long tstride = (long long)T.size() * NT;
+  const long long nP = (long long)r * r, ntot = nP + r;
+  constexpr int EMAX = 4;
+  const bool staged = (r + 1) <= (POOL_DOUBLES - 64);
+  double* Gs = smem_pool();
+  const int rows_per = staged ? max(1, min(len, (POOL_DOUBLES - 64) / (r + 1))) : 1;
+  double* Ds = Gs + (size_t)rows_per * r;
+  for (long long base = 0; base < ntot; base += (long long)EMAX * tstride) {
+    double acc[EMAX];
+#pragma unroll
+    for (int q = 0; q < EMAX; ++q) acc[q] = 0.0;
+    const long long e0 = base + rr_thread(T);
+    for (int jb = a; jb < a + len; jb += rows_per) {
+      const int nr = min(rows_per, a + len - jb);
+      if (staged) {
+        __syncthreads();
+#pragma unroll 8
+        for (int e = threadIdx.x; e < nr * r; e += NT) {
+          const int jj = e / r, i = e - jj * r;
+          Gs[e] = __ldcg(S.G + (size_t)(jb + jj) * rm + i);
+        }
+        for (int e = threadIdx.x; e < nr; e += NT) Ds[e] = __ldcg(S.Dall + jb + e);
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < EMAX; ++q) {
+        const long long e = e0 + (long long)q * tstride;
+        if (e >= ntot) continue;
+        const bool isP = e < nP;
+        const int i = isP ? (int)(e / r) : (int)(e - nP);
+        const int l = isP ? (int)(e - (long long)i * r) : 0;
+        double x0 = 0.0, x1 = 0.0;
+        for (int jj = 0; jj < nr; ++jj) {
+          double gi, gl;
+          if (staged) {
+            gi = Gs[jj * r + i];
+            gl = isP ? Gs[jj * r + l] : Ds[jj];
+          } else {
+            gi = __ldcg(S.G + (size_t)(jb + jj) * rm + i);
+            gl = isP ? __ldcg(S.G + (size_t)(jb + jj) * rm + l) : __ldcg(S.Dall + jb + jj);
+          }
+          if (jj & 1) x1 = fma(gi, gl, x1);
+          else x0 = fma(gi, gl, x0);
+        }
+        acc[q] += x0 + x1;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < EMAX; ++q) {
+      const long long e = e0 + (long long)q * tstride;
+      if (e >= ntot) continue;
+      if (e < nP) {
+        const int i = (int)(e / r), l = (int)(e - (long long)i * r);
+        const size_t o = (size_t)i * rm + l;
+        S.P[o] = __ldcg(S.P + o) + acc[q];
+      } else {
+        const int i = (int)(e - nP);
+        S.u[i] = __ldcg(S.u + i) + acc[q];
+      }
+    }
+  }
+}
+
+// Long runs, step 1: partial Gram sums per chunk of rows; CTA item = (16 x 16 tile pair
+// with ti <= tl, chunk). Diagonal tiles also accumulate sum_j gamma_j D_j for their rows.
+template <class Team>
+__device__ void gram_partials(const Team& T, const StreamDev& S, int a, int len, int r, int nch) {
+  double(*gi_s)[17] = reinterpret_cast<double(*)[17]>(smem_pool());
+  double(*gl_s)[17] = gi_s + 32;
+  double* d_s = reinterpret_cast<double*>(gl_s + 32);
+  const int rm = S.r_max;
+  const int nt = (r + 15) / 16;
+  const int npairs = nt * (nt + 1) / 2;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int per = (len + nch - 1) / nch;
+  for (int it = T.id(); it < npairs * nch; it += T.size()) {
+    const int c = it / npairs;
+    int pr = it - c * npairs, ti = 0;
+    while (pr >= nt - ti) {
+      pr -= nt - ti;
+      ++ti;
+    }
+    const int tl = ti + pr;
+    const int jlo = a + c * per, jhi = min(a + len, jlo + per);
+    double acc = 0.0, uacc = 0.0;
+    for (int jb = jlo; jb < jhi; jb += 32) {
+      __syncthreads();
+#pragma unroll 2
+      for (int e = threadIdx.x; e < 32 * 16; e += NT) {
+        const int jj = e >> 4, cc = e & 15;
+        const int j = jb + jj, i = ti * 16 + cc, l = tl * 16 + cc;
+        gi_s[jj][cc] = (j < jhi && i < r) ? __ldcg(S.G + (size_t)j * rm + i) : 0.0;
+        gl_s[jj][cc] = (j < jhi && l < r) ? __ldcg(S.G + (size_t)j * rm + l) : 0.0;
+      }
+      if (threadIdx.x < 32) d_s[threadIdx.x] = (jb + threadIdx.x < jhi) ? __ldcg(S.Dall + jb + threadIdx.x) : 0.0;
+      __syncthreads();
+#pragma unroll 8
+      for (int jj = 0; jj < 32; ++jj) {
+        acc = fma(gi_s[jj][ty], gl_s[jj][tx], acc);
+        if (tx == 0) uacc = fma(gi_s[jj][ty], d_s[jj], uacc);
+      }
+    }
+    const int i = ti * 16 + ty, l = tl * 16 + tx;
+    double* Pc = S.Pp + (size_t)c * r * r;
+    if (i < r && l < r) Pc[(size_t)i * r + l] = acc;
+    if (ti == tl && tx == 0 && i < r) S.up[(size_t)c * rm + i] = uacc;
+  }
+}
+
+// Long runs, step 2: P += sum_c partials (both triangles), u += sum_c up.
+template <class Team>
+__device__ void gram_reduce(const Team& T, const StreamDev& S, int r, int nch) {
+  const int rm = S.r_max;
+  const long long tstride = (long long)T.size() * NT;
+  const long long nP = (long long)r * r;
+  for (long long e = rr_thread(T); e < nP + r; e += tstride) {
+    if (e < nP) {
+      const int i = (int)(e / r), l = (int)(e - (long long)i * r);
+      const bool upper = (i >> 4) <= (l >> 4);
+      const size_t src = upper ? (size_t)i * r + l : (size_t)l * r + i;
+      double acc = 0.0;
+      for (int c = 0; c < nch; ++c) acc += __ldcg(S.Pp + (size_t)c * r * r + src);
+      const size_t o = (size_t)i * rm + l;
+      S.P[o] = __ldcg(S.P + o) + acc;
+    } else {
+      const int i = (int)(e - nP);
+      double acc = 0.0;
+      for (int c = 0; c < nch; ++c) acc += __ldcg(S.up + (size_t)c * rm + i);
+      S.u[i] = __ldcg(S.u + i) + acc;
+    }
+  }
+}
+
+// A run of dependent rows [a, a + len): short runs directly, long runs through chunked
+// partial sums. Returns false if a team barrier gave up. The caller syncs afterwards.
+template <class Team>
+__device__ bool dep_run(const Team& T, const StreamDev& S, int a, int len, int r) {
+  if (len <= 0 || r == 0) return true;
+  const size_t rr = (size_t)r * r;
+  if (len > SMALL_B && S.Pp && S.pp_cap >= rr) {
+    int nch = (int)min((size_t)NCH_MAX, S.pp_cap / rr);
+    nch = max(1, min(nch, (len + GRAM_CHUNK - 1) / GRAM_CHUNK));
+    gram_partials(T, S, a, len, r, nch);
+    if (!T.sync()) return false;
+    gram_reduce(T, S, r, nch);
+    return true;
+  }
+  acc_small(T, S, a, len, r);
+  return true;
+}
+
+// =======================================================================================
+// Sequential section (worker 0): rows [q0, bend) with FP64 G and R (R row j at
 // S.R[(j - q0) * ld]). Decides each row in order, fixes up the later rows of the section
-// after each append, records segments and the data of every append.
-// ---------------------------------------------------------------------------------------
+// after each append, records the data of every append, extends w_b, and stores for every
+// applied row its a-priori error against w_b as it stands when the row is reached.
+// =======================================================================================
 template <bool ORTHO>
 __device__ void phase_scan(const StreamDev& S, const CallArgs& A, long long j0, int q0, int bend,
                            int r) {
   const int m = S.m, ld = S.ld, rm = S.r_max;
   // dec: 0 dependent, 1 independent, -1 stop (error)
-  __shared__ int nseg, nind, applied, r_cur, dec;
+  __shared__ int nind, applied, r_cur, dec;
   __shared__ double sh_s;
   if (threadIdx.x == 0) {
-    nseg = 0;
     nind = 0;
     applied = bend;
     r_cur = r;
@@ -364,6 +615,11 @@ __device__ void phase_scan(const StreamDev& S, const CallArgs& A, long long j0, 
     const double t = __ldcg(S.t + j);
     const double yv = __ldg(A.y + j0 + j);
     const int rc = r_cur;
+    const double* gj = S.G + (size_t)j * rm;
+    // a-priori error against the current w_b (entries appended in this section included)
+    double dp = 0.0;
+    for (int i = threadIdx.x; i < rc; i += NT) dp = fma(__ldcg(gj + i), __ldcg(S.wb + i), dp);
+    const double dv = yv - block_sum(dp);
     if (threadIdx.x == 0) {
       int d = 0;
       if (!isfinite(t) || !isfinite(yv) || !isfinite(s)) {
@@ -380,21 +636,7 @@ __device__ void phase_scan(const StreamDev& S, const CallArgs& A, long long j0, 
         applied = j;
       } else {
         S.rowflag[j] = (uint8_t)(d + 1);
-        bool extended = false;
-        if (d == 0 && nseg > 0) {
-          int* sg = S.seg + 3 * (nseg - 1);
-          if (sg[0] == SEG_DEP && sg[1] + sg[2] == j) {
-            sg[2] += 1;
-            extended = true;
-          }
-        }
-        if (!extended) {
-          int* nw = S.seg + 3 * nseg;
-          nw[0] = d ? SEG_IND : SEG_DEP;
-          nw[1] = j;
-          nw[2] = 1;
-          nseg += 1;
-        }
+        S.Dall[j] = dv;
       }
       dec = d;
       sh_s = s;
@@ -406,33 +648,60 @@ __device__ void phase_scan(const StreamDev& S, const CallArgs& A, long long j0, 
       const double scale = ORTHO ? 1.0 / sqrt(sh_s) : 1.0 / sh_s;
       double* Kq = S.Kv + (size_t)q * ld;
       for (int c = threadIdx.x; c < m; c += NT) Kq[c] = __ldcg(Rj + c) * scale;
-      const double* gj = S.G + (size_t)j * rm;
       for (int i = threadIdx.x; i < rc; i += NT) S.Gind[(size_t)q * rm + i] = __ldcg(gj + i);
       if (threadIdx.x == 0) {
         S.jind[q] = j;
         S.alpha[q] = 1.0 / sqrt(sh_s);
         S.basis_rows[rc] = base_row + j;
-        if (!ORTHO) {  // general variant: P^-1 <- diag(P^-1, 1), w <- [w; y]
-          for (int i = 0; i < rc; ++i) {
-            S.Pinv[(size_t)rc * rm + i] = 0.0;
-            S.Pinv[(size_t)i * rm + rc] = 0.0;
-          }
-          S.Pinv[(size_t)rc * rm + rc] = 1.0;
-          S.w[rc] = yv;
-        }
+        S.wb[rc] = ORTHO ? 0.0 : yv;  // w_b <- [w_b; y] (general) or [w_b; 0] (orthonormal)
       }
       __syncthreads();
-      const double sj = sh_s, sq = sqrt(sh_s);
-      for (int jt = j + 1; jt < bend; ++jt) {
-        double* Rt = S.R + (size_t)(jt - q0) * ld;
-        double part2 = 0.0;
-        for (int c = threadIdx.x; c < m; c += NT) part2 = fma(__ldcg(Rj + c), __ldcg(Rt + c), part2);
-        const double kap = block_sum(part2) / sj;  // K_j^T Gamma_r,t
-        for (int c = threadIdx.x; c < m; c += NT) Rt[c] = fma(-kap, __ldcg(Rj + c), __ldcg(Rt + c));
-        double* gt = S.G + (size_t)jt * rm;
-        if (!ORTHO)
-          for (int i = threadIdx.x; i < rc; i += NT) gt[i] = fma(-kap, __ldcg(gj + i), __ldcg(gt + i));
-        if (threadIdx.x == 0) gt[rc] = ORTHO ? kap * sq : kap;
+      // fix up every later row of the section at once: kappa_t = K_j^T Gamma_r,t for all
+      // t, then Gamma_r,t -= kappa_t Gamma_r,j and the coordinates of row t gain the new
+      // direction (general: gamma_t -= kappa_t gamma_j, appended kappa_t; orthonormal:
+      // appended kappa_t sqrt(s_j)).
+      const double sq = sqrt(sh_s), isj = 1.0 / sh_s;
+      const int nt = bend - j - 1;
+      if (nt > 0) {
+        double part2[32];
+#pragma unroll
+        for (int tt = 0; tt < 32; ++tt) part2[tt] = 0.0;
+#pragma unroll 4
+        for (int c = threadIdx.x; c < m; c += NT) {
+          const double rj = __ldcg(Rj + c);
+#pragma unroll
+          for (int tt = 0; tt < 32; ++tt)
+            if (tt < nt) part2[tt] = fma(rj, __ldcg(S.R + (size_t)(j + 1 + tt - q0) * ld + c), part2[tt]);
+        }
+        double* red = smem_pool();  // NWARP x 32 partial sums, then kappa
+        const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
+        warp_transpose_sum32(part2);  // lane ln now holds the warp's sum for row ln
+        red[wid * 32 + ln] = part2[0];
+        __syncthreads();
+        if (threadIdx.x < nt) {
+          double a = 0.0;
+          for (int w2 = 0; w2 < NWARP; ++w2) a += red[w2 * 32 + threadIdx.x];
+          red[NWARP * 32 + threadIdx.x] = a * isj;
+        }
+        __syncthreads();
+        const double* kap = red + NWARP * 32;
+#pragma unroll 2
+        for (int c = threadIdx.x; c < m; c += NT) {
+          const double rj = __ldcg(Rj + c);
+          double rt[32];
+#pragma unroll
+          for (int tt = 0; tt < 32; ++tt)
+            rt[tt] = (tt < nt) ? __ldcg(S.R + (size_t)(j + 1 + tt - q0) * ld + c) : 0.0;
+#pragma unroll
+          for (int tt = 0; tt < 32; ++tt)
+            if (tt < nt) S.R[(size_t)(j + 1 + tt - q0) * ld + c] = fma(-kap[tt], rj, rt[tt]);
+        }
+        for (int e = threadIdx.x; e < nt * (rc + 1); e += NT) {
+          const int tt = e / (rc + 1), i = e - tt * (rc + 1);
+          double* gt = S.G + (size_t)(j + 1 + tt) * rm;
+          if (i == rc) gt[rc] = ORTHO ? kap[tt] * sq : kap[tt];
+          else if (!ORTHO) gt[i] = fma(-kap[tt], __ldcg(gj + i), __ldcg(gt + i));
+        }
         __syncthreads();
       }
       if (threadIdx.x == 0) {
@@ -444,47 +713,74 @@ __device__ void phase_scan(const StreamDev& S, const CallArgs& A, long long j0, 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    S.ctrl[CTRL_NSEG] = nseg;
     S.ctrl[CTRL_NIND] = nind;
     S.ctrl[CTRL_APPLIED] = applied;
     S.ctrl[CTRL_RNEW] = r_cur;
   }
 }
 
-// Orthonormal variant, independent row (Section 2.2): with zeta = P^-1 gamma,
-// P^-1 <- [[P^-1, -alpha zeta], [-alpha zeta^T, alpha^2 (1 + gamma^T zeta)]] and
-// w <- [w; alpha (y - gamma^T w)]. CTA 0 only.
-__device__ __forceinline__ void ortho_border(const StreamDev& S, const double* gam, double alpha, double yv, int r) {
+// Apply the sequential section's rows [q0, q0 + napp) to P and u (team-wide, one thread
+// per entry of the new r_new x r_new P and of u). Rows are taken in order with the rank
+// r_j each saw: a dependent row adds gamma_j gamma_j^T on the leading r_j x r_j block and
+// gamma_j D_j to u; an independent row opens entry r_j (general: P_jj = 1; orthonormal:
+// adds g g^T with g = [gamma_j; 1/alpha_j] and g D_j to u).
+template <class Team, bool ORTHO>
+__device__ void section_apply_pu(const Team& T, const StreamDev& S, int q0, int napp, int r,
+                                 int rnew) {
   const int rm = S.r_max;
-  double gz_part = 0.0, gw_part = 0.0;
-  for (int i = threadIdx.x; i < r; i += NT) {
-    double z = 0.0;
-    for (int l = 0; l < r; ++l) z = fma(__ldcg(S.Pinv + (size_t)i * rm + l), __ldcg(gam + l), z);
-    S.Zt[i] = z;  // scratch row 0
-    gz_part = fma(__ldcg(gam + i), z, gz_part);
-    gw_part = fma(__ldcg(gam + i), __ldcg(S.w + i), gw_part);
+  const long long tstride = (long long)T.size() * NT;
+  const long long nP = (long long)rnew * rnew;
+  for (long long e = rr_thread(T); e < nP + rnew; e += tstride) {
+    const bool isP = e < nP;
+    const int i = isP ? (int)(e / rnew) : (int)(e - nP);
+    const int l = isP ? (int)(e - (long long)i * rnew) : 0;
+    double acc = 0.0;
+    int rj = r, q = 0;
+    for (int jj = 0; jj < napp; ++jj) {
+      const int j = q0 + jj;
+      const int flag = __ldcg(S.rowflag + j);
+      const double* g = S.G + (size_t)j * rm;
+      if (flag == 1) {  // dependent
+        if (isP) {
+          if (i < rj && l < rj) acc = fma(__ldcg(g + i), __ldcg(g + l), acc);
+        } else if (i < rj) {
+          acc = fma(__ldcg(g + i), __ldcg(S.Dall + j), acc);
+        }
+      } else {  // independent: opens entry rj
+        if (ORTHO) {
+          const double ia = 1.0 / __ldcg(S.alpha + q);
+          const double gi = (i < rj) ? __ldcg(S.Gind + (size_t)q * rm + i) : (i == rj ? ia : 0.0);
+          if (isP) {
+            const double gl = (l < rj) ? __ldcg(S.Gind + (size_t)q * rm + l) : (l == rj ? ia : 0.0);
+            acc = fma(gi, gl, acc);
+          } else {
+            acc = fma(gi, __ldcg(S.Dall + j), acc);
+          }
+        } else if (isP && i == rj && l == rj) {
+          acc += 1.0;
+        }
+        ++rj;
+        ++q;
+      }
+    }
+    if (isP) {
+      const size_t o = (size_t)i * rm + l;
+      const double base = (i < r && l < r) ? __ldcg(S.P + o) : 0.0;
+      S.P[o] = base + acc;
+    } else {
+      const double base = (i < r) ? __ldcg(S.u + i) : 0.0;
+      S.u[i] = base + acc;
+    }
   }
-  const double gz = block_sum(gz_part);
-  const double gw = block_sum(gw_part);
-  __syncthreads();
-  for (int i = threadIdx.x; i < r; i += NT) {
-    const double v = -alpha * S.Zt[i];
-    S.Pinv[(size_t)i * rm + r] = v;
-    S.Pinv[(size_t)r * rm + i] = v;
-  }
-  if (threadIdx.x == 0) {
-    S.Pinv[(size_t)r * rm + r] = alpha * alpha * (1.0 + gz);
-    S.w[r] = alpha * (yv - gw);
-  }
-  __syncthreads();
 }
 
-// Appends of the sequential section, applied by the whole grid.
+// Appends of the sequential section to the basis, team-wide.
 // General variant: Ct_final[i] = base_i - sum_{q >= qmin(i)} Gind[q][i] K_q with
 // base_i = Ct[i] (i < r) or K_{i-r}, qmin(i) = max(0, i - r + 1); C[r + q] = Gamma_{jind[q]}.
 // Orthonormal variant: Q[r + q] = alpha_q Gamma_r (already scaled in Kv) and its FP32 copy.
 template <class Team, bool ORTHO>
-__device__ void phase_append(const Team& T, const StreamDev& S, const CallArgs& A, long long j0, int r, int nind) {
+__device__ void section_apply_basis(const Team& T, const StreamDev& S, const CallArgs& A, long long j0,
+                                    int r, int nind) {
   const int m = S.m, ld = S.ld, rm = S.r_max;
   const long long gt = (long long)T.id() * NT + threadIdx.x;
   const long long tstride = (long long)T.size() * NT;
@@ -516,12 +812,17 @@ __device__ void phase_append(const Team& T, const StreamDev& S, const CallArgs& 
   }
 }
 
-
-// ---------------------------------------------------------------------------------------
+// =======================================================================================
 // Apply the k rows of one call to one stream, team-wide. Returns false if a bounded team
-// barrier gave up (the status word then holds ST_TIMEOUT). Every worker of the team runs
-// the same control flow; decisions made by worker 0 are read back after a barrier.
-// ---------------------------------------------------------------------------------------
+// barrier gave up (the status word then holds ST_TIMEOUT). Every worker runs the same
+// control flow; values decided by worker 0 are read back after a barrier.
+//
+// Block of b rows: gamma | rejections, norms and a-priori errors | then
+//  * b <= SMALL_B, all rows dependent: every worker decides redundantly and accumulates
+//    into P and u at once (two barriers per block, none after the last block);
+//  * otherwise: worker 0 decides; the dependent run before the first special row is
+//    accumulated; from that row the sequential FP64 section applies the rank changes.
+// =======================================================================================
 template <class Team, bool MIXED>
 __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& A) {
   __shared__ int sh[8];
@@ -537,24 +838,48 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
     const int r = sh[1];
     const int kb0 = sh[2];
     const int b = (int)min((long long)kb0, A.k - j0);
+    const bool last = (j0 + b == A.k);
     const double* gam = A.Gamma + (size_t)j0 * S.m;
     __syncthreads();
-    // 1-2: project every row of the block against the block-start basis
+    // 1: gamma of every row against the block-start basis
+    if (T.id() == 0 && threadIdx.x == 0) S.ctrl[CTRL_Q0] = b;
     phase_gamma<Team, MIXED>(T, S, gam, 0, b, r, MIXED ? S.C : S.Ct);
     if (!T.sync()) return false;
+    // 2: rejections and norms; a-priori errors against w_b
     phase_reject<Team, MIXED>(T, S, gam, 0, b, r, S.C, nullptr);
+    phase_dall(T, S, A, j0, b, r);
     if (!T.sync()) return false;
     // 3: decide
-    if (T.id() == 0) phase_decide<MIXED>(S, A, j0, b, r);
-    if (!T.sync()) return false;
-    if (threadIdx.x == 0) sh[3] = ld_acquire_i32(S.ctrl + CTRL_Q0);
-    __syncthreads();
-    const int q0 = sh[3];
-    // 4: leading dependent run
-    if (q0 > 0 && !woodbury(T, S, A, j0, 0, q0, r)) return false;
+    int q0;
+    if (b <= SMALL_B) {
+      q0 = decide_rows<MIXED>(S, A, j0, b, r, T.id() == 0);
+      if (q0 == b) {  // fast finish: every row dependent
+        acc_small(T, S, 0, b, r);
+        if (T.id() == 0) {
+          if (A.indep)
+            for (int j = threadIdx.x; j < b; j += NT) A.indep[j0 + j] = 0;
+          if (threadIdx.x == 0) {
+            *S.rows_seen = __ldcg(S.rows_seen) + b;
+            S.ctrl[CTRL_KB] = min(2 * kb0, S.kb_max);
+            S.ctrl[CTRL_PEND] = 1;
+          }
+        }
+        if (!last && !T.sync()) return false;
+        j0 += b;
+        continue;
+      }
+    } else {
+      decide_rows_team<Team, MIXED>(T, S, A, j0, b, r);
+      if (!T.sync()) return false;
+      if (threadIdx.x == 0) sh[3] = ld_acquire_i32(S.ctrl + CTRL_Q0);
+      __syncthreads();
+      q0 = sh[3];
+    }
+    // 4: dependent run before the first special row
+    if (q0 > 0 && !dep_run(T, S, 0, q0, r)) return false;
     int applied = b, rnew = r;
     if (q0 < b) {
-      // 5: sequential section, in FP64
+      // 5: sequential section, in FP64 (rows [q0, bend)); its rows never overlap the run
       const int bend = min(b, q0 + SLOW_MAX);
       phase_gamma<Team, false>(T, S, gam, q0, bend, r, MIXED ? S.C : S.Ct);
       if (!T.sync()) return false;
@@ -563,37 +888,16 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       if (T.id() == 0) phase_scan<MIXED>(S, A, j0, q0, bend, r);
       if (!T.sync()) return false;
       if (threadIdx.x == 0) {
-        sh[4] = ld_acquire_i32(S.ctrl + CTRL_NSEG);
         sh[5] = ld_acquire_i32(S.ctrl + CTRL_APPLIED);
         sh[6] = ld_acquire_i32(S.ctrl + CTRL_RNEW);
         sh[7] = ld_acquire_i32(S.ctrl + CTRL_NIND);
       }
       __syncthreads();
-      const int nseg = sh[4];
       applied = sh[5];
       rnew = sh[6];
       const int nind = sh[7];
-      int rs = r, qi = 0;
-      for (int sgi = 0; sgi < nseg; ++sgi) {
-        const int kind = __ldcg(S.seg + 3 * sgi), first = __ldcg(S.seg + 3 * sgi + 1),
-                  cnt = __ldcg(S.seg + 3 * sgi + 2);
-        if (kind == SEG_DEP) {
-          if (!woodbury(T, S, A, j0, first, cnt, rs)) return false;
-        } else {
-          if (MIXED) {
-            if (T.id() == 0)
-              ortho_border(S, S.Gind + (size_t)qi * S.r_max, __ldcg(S.alpha + qi),
-                           __ldg(A.y + j0 + first), rs);
-            if (!T.sync()) return false;
-          }
-          rs += 1;
-          qi += 1;
-        }
-      }
-      if (nind > 0) {
-        phase_append<Team, MIXED>(T, S, A, j0, r, nind);
-        if (!T.sync()) return false;
-      }
+      section_apply_pu<Team, MIXED>(T, S, q0, applied - q0, r, rnew);
+      if (nind > 0) section_apply_basis<Team, MIXED>(T, S, A, j0, r, nind);
     }
     // finalize the block (worker 0): flags, counters, rank, next block size
     if (T.id() == 0) {
@@ -604,12 +908,210 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
         *S.rows_seen = __ldcg(S.rows_seen) + applied;
         S.ctrl[CTRL_R] = rnew;
         S.ctrl[CTRL_KB] = (q0 < b) ? min(KB_MIN, S.kb_max) : min(2 * kb0, S.kb_max);
+        S.ctrl[CTRL_PEND] = 1;
       }
     }
     if (!T.sync()) return false;
     j0 += applied;
   }
   return true;
+}
+
+// =======================================================================================
+// On-demand forms: w = w_b + P^-1 u (solution) and P^-1 (export). Dense helpers for one
+// CTA (all threads): Cholesky of P in the workspace Lw and solves with it.
+// =======================================================================================
+
+// In-place lower Cholesky of A (n x n, row stride lda), 32-wide panels: each diagonal
+// block is factored in shared memory by the whole CTA, the panel below by row-wise
+// substitution, the trailing matrix updated in 32 x 32 tiles. Returns false if a pivot
+// was not positive.
+static __device__ bool cta_cholesky(double* A, int n, int lda) {
+  double* Dk = smem_pool();
+  double(*Pi)[33] = reinterpret_cast<double(*)[33]>(Dk + 32 * 33);
+  double(*Pj)[33] = Pi + 32;
+  __shared__ double invd[32];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int kb = min(32, n - k0);
+    for (int e = threadIdx.x; e < kb * kb; e += NT) {
+      const int i = e / kb, j = e - i * kb;
+      Dk[i * 33 + j] = (j <= i) ? __ldcg(A + (size_t)(k0 + i) * lda + k0 + j) : 0.0;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < kb; ++kk) {
+      if (threadIdx.x == 0) {
+        const double d = Dk[kk * 33 + kk];
+        if (!(d > 0.0) || !isfinite(d)) bad = 1;
+        const double y = rsqrt_nr(fmax(d, 1e-300));
+        Dk[kk * 33 + kk] = d * y;
+        invd[kk] = y;
+      }
+      __syncthreads();
+      const double y = invd[kk];
+      for (int i = kk + 1 + threadIdx.x; i < kb; i += NT) Dk[i * 33 + kk] *= y;
+      __syncthreads();
+      const int rem = kb - kk - 1;
+      for (int e = threadIdx.x; e < rem * rem; e += NT) {
+        const int i = kk + 1 + e / rem, j = kk + 1 + e % rem;
+        if (j <= i) Dk[i * 33 + j] -= Dk[i * 33 + kk] * Dk[j * 33 + kk];
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < kb * kb; e += NT) {
+      const int i = e / kb, j = e - i * kb;
+      if (j <= i) A[(size_t)(k0 + i) * lda + k0 + j] = Dk[i * 33 + j];
+    }
+    // panel below: L[i, k0:k0+kb] = A[i, k0:k0+kb] L_kk^-T (one thread per row)
+    for (int i = k0 + kb + threadIdx.x; i < n; i += NT) {
+      double v[32];
+      double* row = A + (size_t)i * lda + k0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = (j < kb) ? __ldcg(row + j) : 0.0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (j < kb) {
+          double x = v[j];
+          for (int t = 0; t < j; ++t) x -= v[t] * Dk[j * 33 + t];
+          v[j] = x * invd[j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < kb) row[j] = v[j];
+    }
+    __syncthreads();
+    // trailing update A[i][j] -= sum_t L[i][k0+t] L[j][k0+t], lower triangle, 32x32 tiles
+    const int t0 = k0 + kb;
+    const int ntile = (n - t0 + 31) / 32;
+    for (int tt = 0; tt < ntile * ntile; ++tt) {
+      const int bi = tt / ntile, bj = tt - bi * ntile;
+      if (bj > bi) continue;
+      for (int e = threadIdx.x; e < 32 * 32; e += NT) {
+        const int a = e >> 5, t = e & 31;
+        const int ri = t0 + bi * 32 + a, rj = t0 + bj * 32 + a;
+        Pi[a][t] = (ri < n && t < kb) ? __ldcg(A + (size_t)ri * lda + k0 + t) : 0.0;
+        Pj[a][t] = (rj < n && t < kb) ? __ldcg(A + (size_t)rj * lda + k0 + t) : 0.0;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < 32 * 32; e += NT) {
+        const int a = e >> 5, b2 = e & 31;
+        const int ri = t0 + bi * 32 + a, rj = t0 + bj * 32 + b2;
+        if (ri < n && rj < n && rj <= ri) {
+          double acc = 0.0;
+          for (int t = 0; t < kb; ++t) acc = fma(Pi[a][t], Pj[b2][t], acc);
+          double* dst = A + (size_t)ri * lda + rj;
+          *dst = __ldcg(dst) - acc;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  return bad == 0;
+}
+
+// x <- (L L^T)^-1 x for the factor of cta_cholesky; n <= GRAM_RMAX (x staged in shared
+// memory). xin is read with __ldcg, the result goes to xout. Each 32-wide diagonal block
+// is staged in shared memory with the reciprocals of its diagonal (one rsqrt_nr of the
+// squared pivot each), so the sequential steps multiply instead of divide.
+static __device__ void cta_chol_solve(const double* L, int n, int lda, const double* xin,
+                                      double* xout) {
+  __shared__ double dinv[32];
+  double* Db = smem_pool();  // 32 x 33 diagonal block
+  double* xs = Db + 32 * 33;  // n <= GRAM_RMAX entries (fits the pool)
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += NT) xs[i] = __ldcg(xin + i);
+  const int lane = threadIdx.x & 31;
+  for (int pass = 0; pass < 2; ++pass) {  // forward L y = x, then backward L^T z = y
+    const int nblk = (n + 31) / 32;
+    for (int bi = 0; bi < nblk; ++bi) {
+      const int k0 = (pass == 0 ? bi : nblk - 1 - bi) * 32;
+      const int kb = min(32, n - k0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < kb * kb; e += NT) {
+        const int i = e / kb, j = e - i * kb;
+        Db[i * 33 + j] = (j <= i) ? __ldcg(L + (size_t)(k0 + i) * lda + k0 + j) : 0.0;
+      }
+      __syncthreads();
+      if (threadIdx.x < kb) {
+        const double d = Db[threadIdx.x * 33 + threadIdx.x];
+        dinv[threadIdx.x] = rsqrt_nr(d * d);
+      }
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        double v = (lane < kb) ? xs[k0 + lane] : 0.0;
+        if (pass == 0) {
+          for (int p = 0; p < kb; ++p) {
+            const double vp = __shfl_sync(0xffffffffu, v, p) * dinv[p];
+            if (lane == p) v = vp;
+            if (lane > p && lane < kb) v -= Db[lane * 33 + p] * vp;
+          }
+        } else {
+          for (int p = kb - 1; p >= 0; --p) {
+            const double vp = __shfl_sync(0xffffffffu, v, p) * dinv[p];
+            if (lane == p) v = vp;
+            if (lane < p) v -= Db[p * 33 + lane] * vp;
+          }
+        }
+        if (lane < kb) xs[k0 + lane] = v;
+      }
+      __syncthreads();
+      if (pass == 0) {
+        for (int i = k0 + kb + threadIdx.x; i < n; i += NT) {
+          double acc = 0.0;
+          const double* row = L + (size_t)i * lda + k0;
+          for (int t = 0; t < kb; ++t) acc = fma(__ldcg(row + t), xs[k0 + t], acc);
+          xs[i] -= acc;
+        }
+      } else {
+        for (int i = threadIdx.x; i < k0; i += NT) {
+          double acc = 0.0;
+          for (int t = 0; t < kb; ++t) acc = fma(__ldcg(L + (size_t)(k0 + t) * lda + i), xs[k0 + t], acc);
+          xs[i] -= acc;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += NT) xout[i] = xs[i];
+  __syncthreads();
+}
+
+// w = w_b + P^-1 u, by one CTA: Lw = chol(P), then the two triangular solves. Ranks above
+// GRAM_RMAX are refused with ST_BADARG (no shared-memory staging for them).
+static __device__ void form_w(const StreamDev& S, int r) {
+  const int rm = S.r_max;
+  if (r == 0) return;
+  if (r > GRAM_RMAX) {
+    if (threadIdx.x == 0) atomicOr(S.ctrl + CTRL_STATUS, ST_BADARG);
+    return;
+  }
+  for (long long e = threadIdx.x; e < (long long)r * r; e += NT) {
+    const int i = (int)(e / r), l = (int)(e - (long long)i * r);
+    S.Lw[(size_t)i * rm + l] = __ldcg(S.P + (size_t)i * rm + l);
+  }
+  __syncthreads();
+  if (!cta_cholesky(S.Lw, r, rm) && threadIdx.x == 0) atomicOr(S.ctrl + CTRL_STATUS, ST_NONFINITE);
+  cta_chol_solve(S.Lw, r, rm, S.u, S.w);
+  for (int i = threadIdx.x; i < r; i += NT) S.w[i] = __ldcg(S.w + i) + __ldcg(S.wb + i);
+  __syncthreads();
+}
+
+// P^-1 from the factor in Lw (after form_w), team-wide: worker c solves for columns
+// c, c + size, ... (column l of P^-1 = (L L^T)^-1 e_l, stored as row l: P^-1 is symmetric).
+template <class Team>
+__device__ void form_pinv(const Team& T, const StreamDev& S, int r) {
+  const int rm = S.r_max;
+  if (r == 0 || r > GRAM_RMAX) return;
+  for (int l = T.id(); l < r; l += T.size()) {
+    double* out = S.Pinv + (size_t)l * rm;
+    for (int i = threadIdx.x; i < r; i += NT) out[i] = (i == l) ? 1.0 : 0.0;
+    __syncthreads();
+    cta_chol_solve(S.Lw, r, rm, out, out);
+  }
 }
 
 }  // namespace rg

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -103,6 +104,9 @@ size_t carve(StreamDev& S, char* base) {
   S.Ct = S.mixed ? nullptr : cv.take<double>(rm * ld);
   S.Qf = S.mixed ? cv.take<float>(rm * ld) : nullptr;
   S.Pinv = cv.take<double>(rm * rm);
+  S.P = cv.take<double>(rm * rm);
+  S.wb = cv.take<double>(rm);
+  S.u = cv.take<double>(rm);
   S.w = cv.take<double>(rm);
   S.basis_rows = cv.take<long long>(rm);
   S.rows_seen = cv.take<long long>(1);
@@ -118,12 +122,10 @@ size_t carve(StreamDev& S, char* base) {
   S.Gind = cv.take<double>((size_t)SLOW_MAX * rm);
   S.alpha = cv.take<double>(SLOW_MAX);
   S.jind = cv.take<int>(SLOW_MAX);
-  S.seg = cv.take<int>(3 * (SLOW_MAX + 2));
-  S.Zt = cv.take<double>((size_t)SB * rm);
-  S.M = cv.take<double>((size_t)SB * SB);
-  S.Wt = cv.take<double>((size_t)SB * rm);
-  S.D = cv.take<double>(SB);
-  S.aw = cv.take<double>(SB);
+  S.Dall = cv.take<double>(kb);
+  S.Pp = cv.take<double>(S.pp_cap);
+  S.up = cv.take<double>((size_t)NCH_MAX * rm);
+  S.Lw = cv.take<double>(rm * rm);
   return align_up(cv.off, 256);
 }
 
@@ -180,6 +182,10 @@ rg_status rg_init(rg_state** out, int64_t m, double tol, int flags, int64_t r_ma
   long long kb = 4096;
   while (kb > 256 && (double)kb * (double)r_max * 8.0 > 256.0 * (1 << 20)) kb /= 2;
   S.kb_max = (int)kb;
+  {  // Gram-path partials: at least one chunk at full rank, up to NCH_MAX, <= 128 MiB
+    const size_t rr = (size_t)r_max * (size_t)r_max;
+    S.pp_cap = std::max(rr, std::min(rr * NCH_MAX, (size_t)16 << 20));
+  }
   st->arena_bytes = carve(S, nullptr);
   e = cudaMalloc(&st->arena, st->arena_bytes);
   if (e != cudaSuccess) {
@@ -326,7 +332,9 @@ rg_status rg_export(rg_state* st, double* C, double* Ct, double* Pinv, double* w
   if (s != RG_OK && s != RG_ECAPACITY && s != RG_ENONFINITE) return s;
   if (r > capacity) return fail(RG_EINVAL, "rg_export: rank %lld exceeds capacity %lld",
                                 (long long)r, (long long)capacity);
-  cudaError_t e = launch_export(st->S, C, Ct, Pinv, w, (long long*)basis_rows, st->stream);
+  cudaError_t e = cudaSuccess;
+  e = launch_export_prep(st->S, st->grid, st->stream);  // forms w and P^-1 from P
+  if (e == cudaSuccess) e = launch_export(st->S, C, Ct, Pinv, w, (long long*)basis_rows, st->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
   if (e != cudaSuccess) return cuda_fail(e, "rg_export");
   if (rank_out) *rank_out = r;

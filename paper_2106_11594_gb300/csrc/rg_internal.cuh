@@ -10,12 +10,15 @@ namespace rg {
 
 constexpr int NT = 256;          // threads per CTA in every kernel
 constexpr int NWARP = NT / 32;   // warps per CTA
-constexpr int SB = 32;           // rows per blocked Sherman-Morrison (Woodbury) step
+constexpr int SMALL_B = 64;      // blocks up to this many rows take the two-barrier path
 constexpr int SLOW_MAX = 32;     // rows per sequential rank-change section
 constexpr int KB_MIN = 64;       // internal block size right after a rank change
 constexpr int JW = 4;            // observation rows per warp tile in the gamma phase
 constexpr int RJ = 4;            // observation rows per CTA item in the rejection phase
 constexpr int MC = NT / RJ;      // columns per CTA item in the rejection phase (64)
+constexpr int NCH_MAX = 64;      // row chunks of the Gram path
+constexpr int GRAM_CHUNK = 128;  // rows per Gram-path chunk (at least)
+constexpr int GRAM_RMAX = 2048;  // the Gram path is used for ranks up to this
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // bounded waits: 2 s
 
 // Device status bits (mapped to rg_status on the host).
@@ -25,19 +28,15 @@ enum : int { ST_NONFINITE = 1, ST_CAPACITY = 2, ST_TIMEOUT = 4, ST_BADARG = 8 };
 enum : int {
   CTRL_R = 0,          // current rank r
   CTRL_STATUS = 1,     // sticky error bits
-  CTRL_BAR_COUNT = 2,  // grid barrier arrival counter
-  CTRL_BAR_GEN = 3,    // grid barrier generation
+  CTRL_BAR_COUNT = 2,  // grid barrier arrival counter (64 bits: words 2 and 3)
   CTRL_KB = 4,         // adaptive internal block size
   CTRL_Q0 = 5,         // block plan: first row that needs the sequential section
-  CTRL_NSEG = 6,       // block plan: number of segments in the sequential section
   CTRL_APPLIED = 7,    // block plan: rows of the block that were applied
   CTRL_RNEW = 8,       // block plan: rank after the block
   CTRL_NIND = 9,       // block plan: independent rows found in the block
+  CTRL_PEND = 10,      // 1: u holds a correction not yet folded into w
   CTRL_N = 16
 };
-
-// Segment kinds of the sequential section's plan.
-enum : int { SEG_DEP = 0, SEG_IND = 1 };
 
 // Everything a kernel needs to know about one stream. Plain pointers into device
 // memory owned by the host-side rg_state. Two algebraic variants:
@@ -55,8 +54,11 @@ struct StreamDev {
   double* C;      // r_max x ld
   double* Ct;     // r_max x ld (general variant only)
   float* Qf;      // r_max x ld (mixed only)
-  double* Pinv;   // r_max x r_max
-  double* w;      // r_max: X = Ct^T w
+  double* Pinv;   // r_max x r_max: P^-1, formed on demand (export)
+  double* P;      // r_max x r_max: Gram matrix B^T B (information form of P^-1)
+  double* wb;     // r_max: base coordinates w_b
+  double* u;      // r_max: accumulated correction, w = w_b + P^-1 u
+  double* w;      // r_max: w, formed on demand (solution, export); X = Ct^T w
   long long* basis_rows;  // r_max
   long long* rows_seen;   // [1]
   int* ctrl;              // CTRL_N ints
@@ -73,12 +75,11 @@ struct StreamDev {
   double* Gind;   // SLOW_MAX x r_max: gamma (fixed up) of each independent row
   double* alpha;  // SLOW_MAX: orthonormal scale 1/||Gamma_r|| of each independent row
   int* jind;      // SLOW_MAX: block row of each independent row
-  int* seg;       // 3 ints per segment: kind, first row, count
-  double* Zt;     // SB x r_max: zeta_j = P^-1 gamma_j of the current Woodbury step
-  double* M;      // SB x SB: I + G^T P^-1 G
-  double* Wt;     // SB x r_max: L^-1 Z^T
-  double* D;      // SB: a-priori errors y - gamma^T w
-  double* aw;     // SB: M^-1 D
+  double* Dall;   // kb_max: a-priori errors y_j - gamma_j^T w_b of the block's rows
+  double* Pp;     // pp_cap doubles: Gram partials, chunk c at Pp + c * r * r
+  size_t pp_cap;
+  double* up;     // NCH_MAX x r_max: partial sums of gamma_j D_j per chunk
+  double* Lw;     // r_max x r_max: Cholesky workspace (solution, export)
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -108,35 +109,53 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident). The wait is
-// bounded: after WAIT_LIMIT_NS the CTA records ST_TIMEOUT and returns false instead of
-// spinning forever. Works across launches because the last arriver resets the counter.
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident), on a monotonic 64-bit
+// arrival counter (control words CTRL_BAR_COUNT..+1): each CTA adds 1 with a release
+// reduction and waits, with acquire loads, until the counter reaches its next multiple of
+// gridDim.x. grid_barrier_init() must run once per launch before the first barrier; it
+// rounds the counter down to a multiple of gridDim.x (no CTA can have completed a barrier
+// of this launch yet, so at most gridDim.x - 1 early arrivals are rounded away).
+// The wait is bounded: after WAIT_LIMIT_NS the CTA records ST_TIMEOUT and returns false.
+__device__ __forceinline__ unsigned long long& grid_barrier_target() {
+  __shared__ unsigned long long target;
+  return target;
+}
+__device__ __forceinline__ void grid_barrier_init(int* ctrl) {
+  if (threadIdx.x == 0) {
+    const unsigned long long c =
+        ld_acquire_u64(reinterpret_cast<unsigned long long*>(ctrl + CTRL_BAR_COUNT));
+    grid_barrier_target() = (c / gridDim.x) * gridDim.x;
+  }
+  __syncthreads();
+}
 __device__ __forceinline__ bool grid_barrier(int* ctrl) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    unsigned* count = reinterpret_cast<unsigned*>(ctrl + CTRL_BAR_COUNT);
-    unsigned* gen = reinterpret_cast<unsigned*>(ctrl + CTRL_BAR_GEN);
-    const unsigned g = ld_acquire_u32(gen);
-    __threadfence();
-    const unsigned prev = atomicAdd(count, 1u);
-    if (prev == gridDim.x - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ctrl + CTRL_BAR_COUNT);
+    const unsigned long long target = grid_barrier_target() + gridDim.x;
+    grid_barrier_target() = target;
+    red_release_add_u64(cnt, 1ull);
+    if (ld_acquire_u64(cnt) < target) {
       const unsigned long long t0 = global_ns();
-      while (ld_acquire_u32(gen) == g) {
+      while (ld_acquire_u64(cnt) < target) {
         if (global_ns() - t0 > WAIT_LIMIT_NS) {
           atomicOr(ctrl + CTRL_STATUS, ST_TIMEOUT);
           ok = 0;
           break;
         }
-        __nanosleep(40);
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return ok != 0;

@@ -51,7 +51,10 @@ size_t noalloc_layout(StreamDev& S, char* base) {
   S.C = (double*)take(rm * ld * 8);
   S.Ct = S.mixed ? nullptr : (double*)take(rm * ld * 8);
   S.Qf = S.mixed ? (float*)take(rm * ld * 4) : nullptr;
-  S.Pinv = (double*)take(rm * rm * 8);
+  S.Pinv = nullptr;
+  S.P = (double*)take(rm * rm * 8);
+  S.wb = (double*)take(rm * 8);
+  S.u = (double*)take(rm * 8);
   S.w = (double*)take(rm * 8);
   S.basis_rows = (long long*)take(rm * 8);
   S.rows_seen = (long long*)take(8);
@@ -67,12 +70,11 @@ size_t noalloc_layout(StreamDev& S, char* base) {
   S.Gind = (double*)take((size_t)SLOW_MAX * rm * 8);
   S.alpha = (double*)take(SLOW_MAX * 8);
   S.jind = (int*)take(SLOW_MAX * 4);
-  S.seg = (int*)take(3 * (SLOW_MAX + 2) * 4);
-  S.Zt = (double*)take((size_t)SB * rm * 8);
-  S.M = (double*)take((size_t)SB * SB * 8);
-  S.Wt = (double*)take((size_t)SB * rm * 8);
-  S.D = (double*)take(SB * 8);
-  S.aw = (double*)take(SB * 8);
+  S.Dall = (double*)take(kb * 8);
+  S.Lw = (double*)take(rm * rm * 8);
+  S.Pp = nullptr;  // no chunked partial sums here: long runs accumulate directly
+  S.pp_cap = 0;
+  S.up = nullptr;
   return off;
 }
 
@@ -80,6 +82,7 @@ size_t noalloc_layout(StreamDev& S, char* base) {
 
 template <bool MIXED>
 __global__ void __launch_bounds__(NT, 1) noalloc_kernel(StreamDev S, CallArgs A) {
+  grid_barrier_init(S.ctrl);
   process_rows<GridTeam, MIXED>(GridTeam{S.ctrl}, S, A);
 }
 
@@ -94,14 +97,16 @@ __global__ void noalloc_reset_kernel(int* ctrl, long long* rows_seen, int kb0) {
   }
 }
 
-__global__ void noalloc_solution_kernel(StreamDev S, double* X) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= S.m) return;
+// One CTA: w = w_b + P^-1 u, then X = Ct^T w (or Q^T w).
+__global__ void __launch_bounds__(NT, 1) noalloc_solution_kernel(StreamDev S, double* X) {
   const int r = S.ctrl[CTRL_R];
+  form_w(S, r);
   const double* B = S.mixed ? S.C : S.Ct;
-  double acc = 0.0;
-  for (int i = 0; i < r; ++i) acc = fma(B[(size_t)i * S.ld + c], S.w[i], acc);
-  X[c] = acc;
+  for (int c = threadIdx.x; c < S.m; c += NT) {
+    double acc = 0.0;
+    for (int i = 0; i < r; ++i) acc = fma(__ldcg(B + (size_t)i * S.ld + c), __ldcg(S.w + i), acc);
+    X[c] = acc;
+  }
 }
 
 }  // namespace rg
@@ -179,7 +184,7 @@ extern "C" rg_status rg_solve_noalloc(const double* Gamma, const double* y, int6
         dim3(grid), dim3(NT), args, 0, stream);
     if (e != cudaSuccess) return cuda_fail(e, "rg_solve_noalloc: launch");
   }
-  noalloc_solution_kernel<<<(S.m + NT - 1) / NT, NT, 0, stream>>>(S, X);
+  noalloc_solution_kernel<<<1, NT, 0, stream>>>(S, X);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "rg_solve_noalloc: solution launch");
   if (rank_out) {

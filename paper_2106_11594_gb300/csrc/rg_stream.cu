@@ -42,10 +42,14 @@ namespace rg {
 
 template <bool MIXED>
 __global__ void __launch_bounds__(NT, 1) stream_kernel(StreamDev S, CallArgs A) {
+  grid_barrier_init(S.ctrl);
   process_rows<GridTeam, MIXED>(GridTeam{S.ctrl}, S, A);
 }
 
-// X = Ct^T w (general) or Q^T w (orthonormal): one thread per column.
+// w = w_b + P^-1 u (one CTA), then X = Ct^T w (general) or Q^T w (orthonormal).
+__global__ void __launch_bounds__(NT, 1) form_w_kernel(StreamDev S) {
+  form_w(S, S.ctrl[CTRL_R]);
+}
 __global__ void solution_kernel(StreamDev S, double* X) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= S.m) return;
@@ -54,6 +58,16 @@ __global__ void solution_kernel(StreamDev S, double* X) {
   double acc = 0.0;
   for (int i = 0; i < r; ++i) acc = fma(B[(size_t)i * S.ld + c], S.w[i], acc);
   X[c] = acc;
+}
+
+// For an export: w and P^-1 (CTA 0 factors P and forms w, then every CTA solves for some
+// columns of P^-1).
+__global__ void __launch_bounds__(NT, 1) export_prep_kernel(StreamDev S) {
+  grid_barrier_init(S.ctrl);
+  const int r = ld_acquire_i32(S.ctrl + CTRL_R);
+  if (blockIdx.x == 0) form_w(S, r);
+  if (!grid_barrier(S.ctrl)) return;
+  form_pinv(GridTeam{S.ctrl}, S, r);
 }
 
 // Export helpers (compact copies with row stride m / r).
@@ -104,7 +118,15 @@ cudaError_t stream_grid_size(int mixed, int* grid) {
   return cudaSuccess;
 }
 
+cudaError_t launch_export_prep(const StreamDev& S, int grid, cudaStream_t stream) {
+  StreamDev Sc = S;
+  void* args[] = {(void*)&Sc};
+  return cudaLaunchCooperativeKernel((const void*)export_prep_kernel, dim3(grid), dim3(NT), args,
+                                     0, stream);
+}
+
 cudaError_t launch_solution(const StreamDev& S, double* X, cudaStream_t stream) {
+  form_w_kernel<<<1, NT, 0, stream>>>(S);
   solution_kernel<<<(S.m + NT - 1) / NT, NT, 0, stream>>>(S, X);
   return cudaGetLastError();
 }
