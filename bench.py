@@ -53,10 +53,11 @@ def fp64_peak_tflops(sm_mhz: float, nsm: int = 152) -> float:
 
 
 def flops_per_row(m: int, r: int) -> float:
-    """Algorithmic flops of one dependent row: gamma = Ct Gamma (2rm), rejection
-    Gamma - C^T gamma (2rm), ||Gamma_r||^2 and ||Gamma||^2 (4m), zeta = P^-1 gamma (2r^2),
-    P^-1 rank-one update (2r^2), a-priori error and w update (4r)."""
-    return 4.0 * r * m + 4.0 * m + 4.0 * r * r + 4.0 * r
+    """Algorithmic flops of one dependent row as the library computes it: gamma = Ct Gamma
+    (2rm), rejection Gamma - C^T gamma (2rm), ||Gamma_r||^2 and ||Gamma||^2 (4m), the
+    rank-one update of P = B^T B (2r^2), the a-priori error and the correction u (4r).
+    (Algorithm 1's Sherman-Morrison form would count 4r^2 for zeta and P^-1.)"""
+    return 4.0 * r * m + 4.0 * m + 2.0 * r * r + 4.0 * r
 
 
 class ClockSampler:
@@ -229,6 +230,15 @@ def run_gpu(args):
                 ms_k, r_k, _ = timed(mode, k, steps, 1)
                 extra[f"{mname}_k{k if k < n else 'all'}"] = {
                     "rows_per_s": n * steps / (ms_k / 1e3), "ms_per_step": ms_k / steps, "rank": r_k}
+    # --- batched workloads
+    if not args.headline_only and not args.quick:
+        from paper_2106_11594_gb300 import inputs as _inp
+        n3, m3, r3 = _inp.uneven_batch_shapes()
+        shapes3 = [(int(a), int(b), int(c)) for a, b, c in zip(n3, m3, r3)]
+        shapes4 = [(2048, 256, 32)] * 1024
+        for mode, mname in ((rg.RG_MIXED, "mixed"), (rg.RG_FP64, "fp64")):
+            extra[f"batch_uneven4096_{mname}"] = run_batched("uneven", shapes3, 3, 1e-4, mode, 1, 1, dev)
+            extra[f"batch_uniform1024_{mname}"] = run_batched("uniform", shapes4, 4, 1e-3, mode, 1, 1, dev)
     # --- roofline of the dominant kernel (the stream kernel, one launch per 32-row call)
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak = fp64_peak_tflops(sm_mhz)
@@ -255,6 +265,72 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------
+# Batched workloads (extra lines): matrices formed on the GPU from the seeded factors
+# (inputs.factor_stream_factors draws G1, G2, x_true, noise in the generator's order)
+# ---------------------------------------------------------------------------------------
+
+def make_batch_on_gpu(shapes, workload_id, noise, dev):
+    import torch
+
+    from paper_2106_11594_gb300 import inputs
+    n = np.array([s[0] for s in shapes], dtype=np.int64)
+    m = np.array([s[1] for s in shapes], dtype=np.int64)
+    ro = np.zeros(len(shapes) + 1, dtype=np.int64)
+    ro[1:] = np.cumsum(n)
+    eo = np.zeros(len(shapes) + 1, dtype=np.int64)
+    eo[1:] = np.cumsum(n * m)
+    A = torch.empty(int(eo[-1]), dtype=torch.float64, device=dev)
+    Y = torch.empty(int(ro[-1]), dtype=torch.float64, device=dev)
+    for b, (nb, mb, rb) in enumerate(shapes):
+        G1, G2, x, e = inputs.factor_stream_factors(nb, mb, rb, noise, inputs.rng_for(workload_id, b))
+        G1t = torch.from_numpy(G1).to(dev)
+        G2t = torch.from_numpy(G2).to(dev)
+        Ab = G1t @ G2t
+        A[eo[b]:eo[b + 1]] = Ab.reshape(-1)
+        Y[ro[b]:ro[b + 1]] = Ab @ torch.from_numpy(x).to(dev) + torch.from_numpy(e).to(dev)
+    return A, Y, torch.from_numpy(ro).to(dev), torch.from_numpy(eo).to(dev), m
+
+
+def run_batched(name, shapes, workload_id, noise, mode, steps, warmup, dev):
+    import torch
+
+    from paper_2106_11594_gb300 import rg
+    A, Y, ro, eo, m = make_batch_on_gpu(shapes, workload_id, noise, dev)
+    bt = rg.RankGrevilleBatch(m, 1e-10, mode)
+    X = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+    ranks = torch.empty(len(shapes), dtype=torch.int64, device=dev)
+
+    def step():
+        bt.reset()
+        bt.add_rows(A, ro, eo, Y)
+        bt.solution(X, None, ranks)
+
+    for _ in range(warmup):
+        step()
+    bt.sync()
+    stream = torch.cuda.current_stream()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    bt.sync()
+    ms = t0.elapsed_time(t1) / steps
+    rows = int(sum(s[0] for s in shapes))
+    expect = np.array([min(s2) for s2 in shapes])
+    rk = ranks.cpu().numpy()
+    out = {"rows_per_s": rows / (ms / 1e3), "ms_per_step": ms, "rows": rows,
+           "instances": len(shapes), "rank_match_generator": int((rk == expect).sum())}
+    bt.close()
+    del A, Y
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------------------

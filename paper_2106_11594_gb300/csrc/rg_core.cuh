@@ -218,101 +218,150 @@ __device__ void phase_gamma(const Team& T, const StreamDev& S, const double* __r
 }
 
 // Gamma_r = Gamma_j - B^T gamma_j with B = C (general) or Q (orthonormal). CTA item =
-// (RJ rows) x (MC columns), one thread per (row, column). The basis tile (64 ranks x MC
-// columns) and the RJ gamma rows are staged in shared memory per chunk of 64 ranks, so
-// each chunk costs one round of coalesced loads; the sum runs in four chains. Writes
-// per-chunk partial sums of ||Gamma_r||^2 and ||Gamma||^2 and, when Rout != null, the
-// FP64 rejections (row j at Rout[(j - row_lo) * ld]).
-template <class Team, bool F32>
+// (4 RPT rows) x (MC columns): thread (row lane rl, column cc) handles rows rl, rl + 4,
+// ..., so each staged basis tile serves 4 RPT rows. The basis tile (RC ranks x MC
+// columns) and the gamma slice are staged in shared memory per chunk of RC ranks. RPT = 1
+// spreads small blocks over many CTAs; RPT = 8 is used for large blocks. Writes per-chunk
+// partial sums of ||Gamma_r||^2 and ||Gamma||^2 (FP64) and, when Rout != null, the FP64
+// rejections (row j at Rout[(j - row_lo) * ld]).
+template <class Team, bool F32, int RPT>
 __device__ void phase_reject(const Team& T, const StreamDev& S, const double* __restrict__ gam,
                              int row_lo, int row_hi, int r, const double* __restrict__ back64,
                              double* __restrict__ Rout) {
+  using V = typename std::conditional<F32, float, double>::type;
+  constexpr int RB = 4 * RPT;                          // rows per item
+  constexpr int RC = (F32 || RPT == 1) ? 64 : 32;      // ranks per staged chunk
+  static_assert(RC * MC * sizeof(V) / 8 + RB * RC * sizeof(V) / 8 <= POOL_DOUBLES, "pool");
   const int nrows = row_hi - row_lo;
   if (nrows <= 0) return;
-  constexpr int RC = 64;  // ranks per staged chunk
   const int m = S.m, ld = S.ld, nmc = S.nmc, rm = S.r_max;
-  const int ngroups = (nrows + RJ - 1) / RJ;
+  const int ngroups = (nrows + RB - 1) / RB;
   const long long nitems = (long long)ngroups * nmc;
-  __shared__ double red_s[NWARP], red_t[NWARP];
-  double* Bt = smem_pool();     // RC x MC basis tile (FP64 or FP32 values)
-  float* Btf = reinterpret_cast<float*>(Bt);
-  double* Gs = Bt + RC * MC;    // RJ x RC gamma slice
-  const int jj = threadIdx.x / MC;
+  __shared__ double red_s[NWARP][RPT], red_t[NWARP][RPT];
+  V* Bt = reinterpret_cast<V*>(smem_pool());  // RC x MC basis tile
+  V* Gs = Bt + RC * MC;                        // RB x RC gamma slice
   const int cc = threadIdx.x % MC;
+  const int rl = threadIdx.x / MC;             // 0..3
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (long long it = T.id(); it < nitems; it += T.size()) {
     const int grp = (int)(it / nmc);
     const int mc = (int)(it - (long long)grp * nmc);
-    const int j = row_lo + grp * RJ + jj;
+    const int jb = row_lo + grp * RB;
     const int c = mc * MC + cc;
-    const bool valid = (j < row_hi && c < m);
-    const double gv = valid ? __ldg(gam + (size_t)j * m + c) : 0.0;
-    double a0 = gv, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    float f0 = (float)gv, f1 = 0.f;
+    double gv[RPT];
+    V acc[RPT][2];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int j = jb + rl + 4 * q;
+      gv[q] = (j < row_hi && c < m) ? __ldg(gam + (size_t)j * m + c) : 0.0;
+      acc[q][0] = (V)gv[q];
+      acc[q][1] = V(0);
+    }
     for (int i0 = 0; i0 < r; i0 += RC) {
       const int rc = min(RC, r - i0);
       __syncthreads();
-#pragma unroll 16
+#pragma unroll 8
       for (int e = threadIdx.x; e < rc * MC; e += NT) {
         const int ii = e / MC, c2 = mc * MC + (e - ii * MC);
-        if (F32) Btf[e] = (c2 < m) ? __ldcg(S.Qf + (size_t)(i0 + ii) * ld + c2) : 0.f;
-        else Bt[e] = (c2 < m) ? __ldcg(back64 + (size_t)(i0 + ii) * ld + c2) : 0.0;
+        if (F32) Bt[e] = (c2 < m) ? (V)__ldcg(S.Qf + (size_t)(i0 + ii) * ld + c2) : V(0);
+        else Bt[e] = (c2 < m) ? (V)__ldcg(back64 + (size_t)(i0 + ii) * ld + c2) : V(0);
       }
-      float* Gsf = reinterpret_cast<float*>(Gs);
-      for (int e = threadIdx.x; e < RJ * rc; e += NT) {
+#pragma unroll 4
+      for (int e = threadIdx.x; e < RB * rc; e += NT) {
         const int a = e / rc, ii = e - a * rc;
-        const int ja = row_lo + grp * RJ + a;
-        const double gvv = (ja < row_hi) ? __ldcg(S.G + (size_t)ja * rm + i0 + ii) : 0.0;
-        if (F32) Gsf[a * RC + ii] = (float)gvv;
-        else Gs[a * RC + ii] = gvv;
+        const int ja = jb + a;
+        Gs[a * RC + ii] = (ja < row_hi) ? (V)__ldcg(S.G + (size_t)ja * rm + i0 + ii) : V(0);
       }
       __syncthreads();
-      const double* g = Gs + jj * RC;
-      if (F32) {
-        const float* gf = Gsf + jj * RC;
-        int ii = 0;
-        for (; ii + 1 < rc; ii += 2) {
-          f0 = fmaf(-Btf[ii * MC + cc], gf[ii], f0);
-          f1 = fmaf(-Btf[(ii + 1) * MC + cc], gf[ii + 1], f1);
+      int ii = 0;
+      for (; ii + 1 < rc; ii += 2) {
+        const V b0 = Bt[ii * MC + cc], b1 = Bt[(ii + 1) * MC + cc];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          const V* g = Gs + (rl + 4 * q) * RC;
+          acc[q][0] = fma(-b0, g[ii], acc[q][0]);
+          acc[q][1] = fma(-b1, g[ii + 1], acc[q][1]);
         }
-        if (ii < rc) f0 = fmaf(-Btf[ii * MC + cc], gf[ii], f0);
-      } else {
-        int ii = 0;
-        for (; ii + 3 < rc; ii += 4) {
-          a0 = fma(-Bt[ii * MC + cc], g[ii], a0);
-          a1 = fma(-Bt[(ii + 1) * MC + cc], g[ii + 1], a1);
-          a2 = fma(-Bt[(ii + 2) * MC + cc], g[ii + 2], a2);
-          a3 = fma(-Bt[(ii + 3) * MC + cc], g[ii + 3], a3);
-        }
-        for (; ii < rc; ++ii) a0 = fma(-Bt[ii * MC + cc], g[ii], a0);
+      }
+      if (ii < rc) {
+        const V b0 = Bt[ii * MC + cc];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) acc[q][0] = fma(-b0, Gs[(rl + 4 * q) * RC + ii], acc[q][0]);
       }
     }
-    double sv = 0.0, tv = 0.0;
-    if (valid) {
-      if (F32) {
-        const float acc = f0 + f1;
-        sv = (double)acc * (double)acc;
-      } else {
-        const double acc = (a0 + a1) + (a2 + a3);
-        sv = acc * acc;
-        if (Rout) Rout[(size_t)(j - row_lo) * ld + c] = acc;
-      }
-      tv = gv * gv;
+    double sv[RPT], tv[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int j = jb + rl + 4 * q;
+      const bool valid = (j < row_hi && c < m);
+      const V a = acc[q][0] + acc[q][1];
+      sv[q] = valid ? (double)a * (double)a : 0.0;
+      tv[q] = valid ? gv[q] * gv[q] : 0.0;
+      if (!F32 && Rout && valid) Rout[(size_t)(j - row_lo) * ld + c] = (double)a;
     }
-    sv = warp_sum(sv);
-    tv = warp_sum(tv);
-    __syncthreads();
-    if (lane == 0) {
-      red_s[warp] = sv;
-      red_t[warp] = tv;
+    // per warp: the 32 columns of its row lane; lanes reduce the RPT rows at once
+    double ts, tt;
+    int qi = 0;
+    if (RPT == 1) {
+      ts = warp_sum(sv[0]);
+      tt = warp_sum(tv[0]);
+    } else {
+      ts = warp_transpose_sum<double, RPT>(sv);
+      tt = warp_transpose_sum<double, RPT>(tv);
+      qi = transpose_sum_index<RPT>();
     }
     __syncthreads();
-    if (threadIdx.x < RJ) {  // MC = 64 columns per row = 2 warps per row
-      const int jr = row_lo + grp * RJ + threadIdx.x;
+    if ((lane & (32 / RPT - 1)) == 0) {
+      red_s[warp][qi] = ts;
+      red_t[warp][qi] = tt;
+    }
+    __syncthreads();
+    if (threadIdx.x < RB) {  // row a = rl + 4 q: warps 2 rl and 2 rl + 1 hold its columns
+      const int a = threadIdx.x, rla = a & 3, q = a >> 2;
+      const int jr = jb + a;
       if (jr < row_hi) {
-        S.spart[(size_t)jr * nmc + mc] = red_s[2 * threadIdx.x] + red_s[2 * threadIdx.x + 1];
-        S.tpart[(size_t)jr * nmc + mc] = red_t[2 * threadIdx.x] + red_t[2 * threadIdx.x + 1];
+        S.spart[(size_t)jr * nmc + mc] = red_s[2 * rla][q] + red_s[2 * rla + 1][q];
+        S.tpart[(size_t)jr * nmc + mc] = red_t[2 * rla][q] + red_t[2 * rla + 1][q];
       }
+    }
+  }
+}
+
+// Mixed mode, large blocks: gamma with the block's rows staged once in shared memory,
+// converted to FP32 (CTA item = GR rows x all basis rows; warp w takes basis rows
+// w, w + NWARP, ...; lanes stride over the columns; FP32 accumulation).
+template <class Team>
+__device__ void phase_gamma_f32_staged(const Team& T, const StreamDev& S, const double* __restrict__ gam,
+                                       int row_lo, int row_hi, int r, int GR) {
+  const int m = S.m, ld = S.ld, rm = S.r_max;
+  float* Gf = reinterpret_cast<float*>(smem_pool());  // GR x m
+  const int ngroups = (row_hi - row_lo + GR - 1) / GR;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int it = T.id(); it < ngroups; it += T.size()) {
+    const int j0 = row_lo + it * GR;
+    const int nj = min(GR, row_hi - j0);
+    __syncthreads();
+#pragma unroll 8
+    for (int e = threadIdx.x; e < GR * m; e += NT) {
+      const int a = e / m, c = e - a * m;
+      Gf[e] = (a < nj) ? (float)__ldg(gam + (size_t)(j0 + a) * m + c) : 0.f;
+    }
+    __syncthreads();
+    for (int i = warp; i < r; i += NWARP) {
+      const float* q = S.Qf + (size_t)i * ld;
+      float acc[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) acc[a] = 0.f;
+#pragma unroll 4
+      for (int c = lane; c < m; c += 32) {
+        const float qv = __ldcg(q + c);
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+          if (a < GR) acc[a] = fmaf(qv, Gf[a * m + c], acc[a]);
+      }
+      const float tot = warp_transpose_sum<float, 8>(acc);
+      const int a = transpose_sum_index<8>();
+      if ((lane & 3) == 0 && a < nj) S.G[(size_t)(j0 + a) * rm + i] = (double)tot;
     }
   }
 }
@@ -843,10 +892,17 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
     __syncthreads();
     // 1: gamma of every row against the block-start basis
     if (T.id() == 0 && threadIdx.x == 0) S.ctrl[CTRL_Q0] = b;
-    phase_gamma<Team, MIXED>(T, S, gam, 0, b, r, MIXED ? S.C : S.Ct);
+    // larger items only while they still give every worker at least two
+    const bool big_rej = (long long)(b / 32) * S.nmc >= 2LL * T.size();
+    const int gr = min(8, (int)((POOL_DOUBLES * 2) / max(S.m, 1)));  // FP32 rows that fit
+    if (MIXED && gr >= 1 && (long long)(b / gr) >= 2LL * T.size())
+      phase_gamma_f32_staged(T, S, gam, 0, b, r, gr);
+    else
+      phase_gamma<Team, MIXED>(T, S, gam, 0, b, r, MIXED ? S.C : S.Ct);
     if (!T.sync()) return false;
     // 2: rejections and norms; a-priori errors against w_b
-    phase_reject<Team, MIXED>(T, S, gam, 0, b, r, S.C, nullptr);
+    if (big_rej) phase_reject<Team, MIXED, 8>(T, S, gam, 0, b, r, S.C, nullptr);
+    else phase_reject<Team, MIXED, 1>(T, S, gam, 0, b, r, S.C, nullptr);
     phase_dall(T, S, A, j0, b, r);
     if (!T.sync()) return false;
     // 3: decide
@@ -883,7 +939,7 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       const int bend = min(b, q0 + SLOW_MAX);
       phase_gamma<Team, false>(T, S, gam, q0, bend, r, MIXED ? S.C : S.Ct);
       if (!T.sync()) return false;
-      phase_reject<Team, false>(T, S, gam, q0, bend, r, S.C, S.R);
+      phase_reject<Team, false, 1>(T, S, gam, q0, bend, r, S.C, S.R);
       if (!T.sync()) return false;
       if (T.id() == 0) phase_scan<MIXED>(S, A, j0, q0, bend, r);
       if (!T.sync()) return false;
