@@ -96,7 +96,10 @@ __host__ __device__ inline size_t scratch_layout(int kb, int ldm, int rmm, int n
   char* Pp = take((size_t)rmm * rmm * 8);  // one chunk: a CTA team gains nothing from more
   char* up = take((size_t)NCH_MAX * rmm * 8);
   char* Lw = take((size_t)rmm * rmm * 8);
+  char* Sp = take((size_t)2 * 32 * 8);  // one worker (the CTA)
   if (S) {
+    S->Sp = (double*)Sp;
+    S->sp_stride = 32;
     S->Dall = (double*)Dall;
     S->Pp = (double*)Pp;
     S->pp_cap = (size_t)rmm * rmm;

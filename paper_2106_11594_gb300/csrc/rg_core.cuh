@@ -634,138 +634,137 @@ __device__ bool dep_run(const Team& T, const StreamDev& S, int a, int len, int r
 }
 
 // =======================================================================================
-// Sequential section (worker 0): rows [q0, bend) with FP64 G and R (R row j at
-// S.R[(j - q0) * ld]). Decides each row in order, fixes up the later rows of the section
-// after each append, records the data of every append, extends w_b, and stores for every
-// applied row its a-priori error against w_b as it stands when the row is reached.
+// Sequential section, team-wide: rows [q0, bend) with FP64 G and R (R row j at
+// S.R[(j - q0) * ld]). Rows are decided in order; after each append the later rows of the
+// section are fixed up (their rejections lose the new direction:
+// Gamma_r,t -= kappa_t Gamma_r,j, kappa_t = K_j^T Gamma_r,t). Every worker owns a slice of
+// the columns; per row one pass computes the partial ||Gamma_r,j||^2 and the partial dot
+// products with all later rows of the section, the partials are exchanged through S.Sp
+// (double-buffered by row parity) across one team barrier and summed by every worker in
+// the same order, so all workers take the same decision. S.Sp holds, per parity,
+// 32 partials for each of the first min(workers, ceil(m / NT)) workers. Worker 0 keeps the bookkeeping:
+// the data of each append, w_b, the rank-row record, the flags and, for every applied row,
+// its a-priori error against w_b as it stands when the row is reached.
+// Returns false if a barrier gave up; out = {applied, r_new, n_ind}.
 // =======================================================================================
-template <bool ORTHO>
-__device__ void phase_scan(const StreamDev& S, const CallArgs& A, long long j0, int q0, int bend,
-                           int r) {
+template <class Team, bool ORTHO>
+__device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, long long j0, int q0,
+                          int bend, int r, int out[3]) {
   const int m = S.m, ld = S.ld, rm = S.r_max;
-  // dec: 0 dependent, 1 independent, -1 stop (error)
-  __shared__ int nind, applied, r_cur, dec;
-  __shared__ double sh_s;
-  if (threadIdx.x == 0) {
-    nind = 0;
-    applied = bend;
-    r_cur = r;
-  }
-  __syncthreads();
+  const long long col0 = (long long)T.id() * NT + threadIdx.x;
+  const long long cstride = (long long)T.size() * NT;
+  __shared__ double tot[32];
+  __shared__ double wred[NWARP][32];
+  __shared__ int dec_s;
+  __shared__ double dv_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // workers that own columns (the column slices are NT wide); only they publish partials
+  const int nact = (int)min((long long)T.size(), ((long long)m + NT - 1) / NT);
+  int rc = r, nind = 0, applied = bend;
   const long long base_row = __ldcg(S.rows_seen);
   for (int j = q0; j < bend; ++j) {
+    const int nt = bend - j - 1;
     const double* Rj = S.R + (size_t)(j - q0) * ld;
-    double part = 0.0;
-    for (int c = threadIdx.x; c < m; c += NT) {
-      const double v = __ldcg(Rj + c);
-      part = fma(v, v, part);
+    // partials over my columns: v[0] = ||R_j||^2, v[1 + t] = R_j . R_{j+1+t}
+    double v[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = 0.0;
+    for (long long c = col0; c < m; c += cstride) {
+      const double rj = __ldcg(Rj + c);
+      v[0] = fma(rj, rj, v[0]);
+#pragma unroll
+      for (int t = 0; t < 31; ++t)
+        if (t < nt) v[1 + t] = fma(rj, __ldcg(S.R + (size_t)(j + 1 + t - q0) * ld + c), v[1 + t]);
     }
-    const double s = block_sum(part);  // ||Gamma_r||^2 after the in-block fix-ups
-    const double t = __ldcg(S.t + j);
-    const double yv = __ldg(A.y + j0 + j);
-    const int rc = r_cur;
-    const double* gj = S.G + (size_t)j * rm;
-    // a-priori error against the current w_b (entries appended in this section included)
+    warp_transpose_sum32(v);  // lane l holds the warp's sum of value l
+    wred[warp][lane] = v[0];
+    __syncthreads();
+    double* Sp = S.Sp + (size_t)(j & 1) * S.sp_stride;
+    if (T.id() < nact && threadIdx.x < 32) {
+      double a = 0.0;
+#pragma unroll
+      for (int w2 = 0; w2 < NWARP; ++w2) a += wred[w2][threadIdx.x];
+      Sp[(size_t)T.id() * 32 + threadIdx.x] = a;
+    }
+    // worker 0: the a-priori error of row j against the current w_b
     double dp = 0.0;
-    for (int i = threadIdx.x; i < rc; i += NT) dp = fma(__ldcg(gj + i), __ldcg(S.wb + i), dp);
-    const double dv = yv - block_sum(dp);
-    if (threadIdx.x == 0) {
-      int d = 0;
-      if (!isfinite(t) || !isfinite(yv) || !isfinite(s)) {
-        atomicOr(S.ctrl + CTRL_STATUS, ST_NONFINITE);
-        d = -1;
-      } else if (is_independent(s, t, rc, m, S.tol, S.test_mode)) {
-        d = 1;
-        if (rc >= rm) {
-          atomicOr(S.ctrl + CTRL_STATUS, ST_CAPACITY);
-          d = -1;
-        }
-      }
-      if (d < 0) {
-        applied = j;
-      } else {
-        S.rowflag[j] = (uint8_t)(d + 1);
-        S.Dall[j] = dv;
-      }
-      dec = d;
-      sh_s = s;
+    if (T.id() == 0) {
+      const double* gj = S.G + (size_t)j * rm;
+      for (int i = threadIdx.x; i < rc; i += NT) dp = fma(__ldcg(gj + i), __ldcg(S.wb + i), dp);
+      dp = block_sum(dp);
+      if (threadIdx.x == 0) dv_s = __ldg(A.y + j0 + j) - dp;
+    }
+    if (!T.sync()) return false;
+    // every worker sums the partials in the same order
+    if (threadIdx.x < 32) {
+      double a = 0.0;
+      for (int w2 = 0; w2 < nact; ++w2) a += __ldcg(Sp + (size_t)w2 * 32 + threadIdx.x);
+      tot[threadIdx.x] = a;
     }
     __syncthreads();
-    if (dec < 0) break;
-    if (dec == 1) {  // independent row: record the append, fix up the later rows
+    const double s = tot[0];
+    const double t = __ldcg(S.t + j);
+    const double yv = __ldg(A.y + j0 + j);
+    if (threadIdx.x == 0) {
+      int d = 0;
+      if (!isfinite(t) || !isfinite(yv) || !isfinite(s)) d = -1;
+      else if (is_independent(s, t, rc, m, S.tol, S.test_mode)) d = (rc >= rm) ? -2 : 1;
+      dec_s = d;
+    }
+    __syncthreads();
+    const int d = dec_s;
+    if (d < 0) {
+      if (T.id() == 0 && threadIdx.x == 0)
+        atomicOr(S.ctrl + CTRL_STATUS, d == -1 ? ST_NONFINITE : ST_CAPACITY);
+      applied = j;
+      break;
+    }
+    if (T.id() == 0 && threadIdx.x == 0) {
+      S.rowflag[j] = (uint8_t)(d + 1);
+      S.Dall[j] = dv_s;
+    }
+    if (d == 1) {  // independent: record the append, fix up the later rows
       const int q = nind;
-      const double scale = ORTHO ? 1.0 / sqrt(sh_s) : 1.0 / sh_s;
+      const double scale = ORTHO ? 1.0 / sqrt(s) : 1.0 / s;
+      const double is = 1.0 / s, sq = sqrt(s);
       double* Kq = S.Kv + (size_t)q * ld;
-      for (int c = threadIdx.x; c < m; c += NT) Kq[c] = __ldcg(Rj + c) * scale;
-      for (int i = threadIdx.x; i < rc; i += NT) S.Gind[(size_t)q * rm + i] = __ldcg(gj + i);
-      if (threadIdx.x == 0) {
-        S.jind[q] = j;
-        S.alpha[q] = 1.0 / sqrt(sh_s);
-        S.basis_rows[rc] = base_row + j;
-        S.wb[rc] = ORTHO ? 0.0 : yv;  // w_b <- [w_b; y] (general) or [w_b; 0] (orthonormal)
+      for (long long c = col0; c < m; c += cstride) {
+        const double rj = __ldcg(Rj + c);
+        Kq[c] = rj * scale;
+#pragma unroll
+        for (int tt = 0; tt < 31; ++tt)
+          if (tt < nt) {
+            double* Rt = S.R + (size_t)(j + 1 + tt - q0) * ld;
+            Rt[c] = fma(-tot[1 + tt] * is, rj, __ldcg(Rt + c));
+          }
       }
-      __syncthreads();
-      // fix up every later row of the section at once: kappa_t = K_j^T Gamma_r,t for all
-      // t, then Gamma_r,t -= kappa_t Gamma_r,j and the coordinates of row t gain the new
-      // direction (general: gamma_t -= kappa_t gamma_j, appended kappa_t; orthonormal:
-      // appended kappa_t sqrt(s_j)).
-      const double sq = sqrt(sh_s), isj = 1.0 / sh_s;
-      const int nt = bend - j - 1;
-      if (nt > 0) {
-        double part2[32];
-#pragma unroll
-        for (int tt = 0; tt < 32; ++tt) part2[tt] = 0.0;
-#pragma unroll 4
-        for (int c = threadIdx.x; c < m; c += NT) {
-          const double rj = __ldcg(Rj + c);
-#pragma unroll
-          for (int tt = 0; tt < 32; ++tt)
-            if (tt < nt) part2[tt] = fma(rj, __ldcg(S.R + (size_t)(j + 1 + tt - q0) * ld + c), part2[tt]);
+      if (T.id() == 0) {
+        const double* gj = S.G + (size_t)j * rm;
+        for (int i = threadIdx.x; i < rc; i += NT) S.Gind[(size_t)q * rm + i] = __ldcg(gj + i);
+        if (threadIdx.x == 0) {
+          S.jind[q] = j;
+          S.alpha[q] = 1.0 / sq;
+          S.basis_rows[rc] = base_row + j;
+          S.wb[rc] = ORTHO ? 0.0 : yv;  // w_b <- [w_b; y] (general) or [w_b; 0] (orthonormal)
         }
-        double* red = smem_pool();  // NWARP x 32 partial sums, then kappa
-        const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
-        warp_transpose_sum32(part2);  // lane ln now holds the warp's sum for row ln
-        red[wid * 32 + ln] = part2[0];
-        __syncthreads();
-        if (threadIdx.x < nt) {
-          double a = 0.0;
-          for (int w2 = 0; w2 < NWARP; ++w2) a += red[w2 * 32 + threadIdx.x];
-          red[NWARP * 32 + threadIdx.x] = a * isj;
-        }
-        __syncthreads();
-        const double* kap = red + NWARP * 32;
-#pragma unroll 2
-        for (int c = threadIdx.x; c < m; c += NT) {
-          const double rj = __ldcg(Rj + c);
-          double rt[32];
-#pragma unroll
-          for (int tt = 0; tt < 32; ++tt)
-            rt[tt] = (tt < nt) ? __ldcg(S.R + (size_t)(j + 1 + tt - q0) * ld + c) : 0.0;
-#pragma unroll
-          for (int tt = 0; tt < 32; ++tt)
-            if (tt < nt) S.R[(size_t)(j + 1 + tt - q0) * ld + c] = fma(-kap[tt], rj, rt[tt]);
-        }
+        // coordinates of the later rows gain the new direction
         for (int e = threadIdx.x; e < nt * (rc + 1); e += NT) {
           const int tt = e / (rc + 1), i = e - tt * (rc + 1);
           double* gt = S.G + (size_t)(j + 1 + tt) * rm;
-          if (i == rc) gt[rc] = ORTHO ? kap[tt] * sq : kap[tt];
-          else if (!ORTHO) gt[i] = fma(-kap[tt], __ldcg(gj + i), __ldcg(gt + i));
+          const double kap = tot[1 + tt] * is;
+          if (i == rc) gt[rc] = ORTHO ? kap * sq : kap;
+          else if (!ORTHO) gt[i] = fma(-kap, __ldcg(gj + i), __ldcg(gt + i));
         }
         __syncthreads();
       }
-      if (threadIdx.x == 0) {
-        nind = q + 1;
-        r_cur = rc + 1;
-      }
-      __syncthreads();
+      ++rc;
+      ++nind;
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    S.ctrl[CTRL_NIND] = nind;
-    S.ctrl[CTRL_APPLIED] = applied;
-    S.ctrl[CTRL_RNEW] = r_cur;
-  }
+  out[0] = applied;
+  out[1] = rc;
+  out[2] = nind;
+  return true;
 }
 
 // Apply the sequential section's rows [q0, q0 + napp) to P and u (team-wide, one thread
@@ -941,17 +940,12 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       if (!T.sync()) return false;
       phase_reject<Team, false, 1>(T, S, gam, q0, bend, r, S.C, S.R);
       if (!T.sync()) return false;
-      if (T.id() == 0) phase_scan<MIXED>(S, A, j0, q0, bend, r);
+      int res[3];
+      if (!scan_team<Team, MIXED>(T, S, A, j0, q0, bend, r, res)) return false;
       if (!T.sync()) return false;
-      if (threadIdx.x == 0) {
-        sh[5] = ld_acquire_i32(S.ctrl + CTRL_APPLIED);
-        sh[6] = ld_acquire_i32(S.ctrl + CTRL_RNEW);
-        sh[7] = ld_acquire_i32(S.ctrl + CTRL_NIND);
-      }
-      __syncthreads();
-      applied = sh[5];
-      rnew = sh[6];
-      const int nind = sh[7];
+      applied = res[0];
+      rnew = res[1];
+      const int nind = res[2];
       section_apply_pu<Team, MIXED>(T, S, q0, applied - q0, r, rnew);
       if (nind > 0) section_apply_basis<Team, MIXED>(T, S, A, j0, r, nind);
     }

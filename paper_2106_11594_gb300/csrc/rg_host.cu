@@ -126,6 +126,8 @@ size_t carve(StreamDev& S, char* base) {
   S.Pp = cv.take<double>(S.pp_cap);
   S.up = cv.take<double>((size_t)NCH_MAX * rm);
   S.Lw = cv.take<double>(rm * rm);
+  S.sp_stride = (size_t)32 * std::min<size_t>((ld + NT - 1) / NT, 1024);  // <= 1024 workers
+  S.Sp = cv.take<double>(2 * S.sp_stride);
   return align_up(cv.off, 256);
 }
 

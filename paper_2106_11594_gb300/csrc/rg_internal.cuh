@@ -80,6 +80,8 @@ struct StreamDev {
   size_t pp_cap;
   double* up;     // NCH_MAX x r_max: partial sums of gamma_j D_j per chunk
   double* Lw;     // r_max x r_max: Cholesky workspace (solution, export)
+  double* Sp;     // 2 x sp_stride: per-worker partial sums of the sequential section
+  size_t sp_stride;  // >= 32 x (number of workers)
 };
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -72,6 +72,8 @@ size_t noalloc_layout(StreamDev& S, char* base) {
   S.jind = (int*)take(SLOW_MAX * 4);
   S.Dall = (double*)take(kb * 8);
   S.Lw = (double*)take(rm * rm * 8);
+  S.sp_stride = (size_t)32 * std::min<size_t>((ld + NT - 1) / NT, 1024);  // <= 1024 workers
+  S.Sp = (double*)take(2 * S.sp_stride * 8);
   S.Pp = nullptr;  // no chunked partial sums here: long runs accumulate directly
   S.pp_cap = 0;
   S.up = nullptr;
@@ -164,8 +166,8 @@ extern "C" rg_status rg_solve_noalloc(const double* Gamma, const double* y, int6
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, noalloc_kernel<true>, NT, 0);
       if (e != cudaSuccess) return cuda_fail(e, "rg_solve_noalloc: occupancy query");
       if (per0 < 1 || per1 < 1) return fail(RG_ECUDA, "rg_solve_noalloc: kernel cannot be resident");
-      g_noalloc_grid[0][dev] = nsm;
-      g_noalloc_grid[1][dev] = nsm;
+      g_noalloc_grid[0][dev] = std::min(nsm, 1024);
+      g_noalloc_grid[1][dev] = std::min(nsm, 1024);
       g_noalloc_ptr[dev] = p;
     }
     base = g_noalloc_ptr[dev];

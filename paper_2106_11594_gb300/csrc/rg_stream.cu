@@ -34,6 +34,8 @@
 // Ct = C = Q), projects in FP32 against an FP32 copy of Q, and re-decides every row whose
 // FP32 relative rejection exceeds the floor tau_lo in FP64.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "rg_core.cuh"
@@ -114,7 +116,7 @@ cudaError_t stream_grid_size(int mixed, int* grid) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &per, mixed ? (const void*)stream_kernel<true> : (const void*)stream_kernel<false>, NT, 0);
   if (e != cudaSuccess) return e;
-  *grid = nsm * (per >= 1 ? 1 : 0);
+  *grid = std::min(nsm, 1024) * (per >= 1 ? 1 : 0);  // the section scan holds <= 1024 workers
   return cudaSuccess;
 }
 
