@@ -131,6 +131,7 @@ def dist_env():
 def run_gpu(args):
     import torch
 
+    from paper_2106_11594_gb300 import dist as rgdist
     from paper_2106_11594_gb300 import inputs, rg
 
     ws, rank, local = dist_env()
@@ -174,6 +175,8 @@ def run_gpu(args):
             one_step(st, k, ev)
         t1.record(stream)
         torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
         ms = t0.elapsed_time(t1)
         st.sync()
         r = st.rank()
@@ -187,12 +190,10 @@ def run_gpu(args):
     with ClockSampler(local) as clk:
         ms, rk, launch_ms = timed(rg.RG_FP64, K_CALL, args.steps, args.warmup, launch_events=True)
     clocks = clk.summary()
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    # one replica of the stream per rank (a single stream does not shard): whole-job rows
+    # over the slowest rank's time
+    value, ms, _ = rgdist.job_throughput(n * args.steps, ms, dev)
     ms_per_step = ms / args.steps
-    value = ws * n * args.steps / (ms / 1e3)
     # parity of the last step against the oracle is covered by the tests; report the rank
     # --- e2e through host buffers (pinned), copies inside the timed region
     e2e = None
@@ -237,8 +238,8 @@ def run_gpu(args):
         shapes3 = [(int(a), int(b), int(c)) for a, b, c in zip(n3, m3, r3)]
         shapes4 = [(2048, 256, 32)] * 1024
         for mode, mname in ((rg.RG_MIXED, "mixed"), (rg.RG_FP64, "fp64")):
-            extra[f"batch_uneven4096_{mname}"] = run_batched("uneven", shapes3, 3, 1e-4, mode, 1, 1, dev)
-            extra[f"batch_uniform1024_{mname}"] = run_batched("uniform", shapes4, 4, 1e-3, mode, 1, 1, dev)
+            extra[f"batch_uneven4096_{mname}"] = run_batched("uneven", shapes3, 3, 1e-4, mode, 1, 1, dev, ws, rank)
+            extra[f"batch_uniform1024_{mname}"] = run_batched("uniform", shapes4, 4, 1e-3, mode, 1, 1, dev, ws, rank)
     # --- roofline of the dominant kernel (the stream kernel, one launch per 32-row call)
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak = fp64_peak_tflops(sm_mhz)
@@ -272,7 +273,7 @@ def run_gpu(args):
 # (inputs.factor_stream_factors draws G1, G2, x_true, noise in the generator's order)
 # ---------------------------------------------------------------------------------------
 
-def make_batch_on_gpu(shapes, workload_id, noise, dev):
+def make_batch_on_gpu(shapes, workload_id, noise, dev, ids=None):
     import torch
 
     from paper_2106_11594_gb300 import inputs
@@ -284,8 +285,9 @@ def make_batch_on_gpu(shapes, workload_id, noise, dev):
     eo[1:] = np.cumsum(n * m)
     A = torch.empty(int(eo[-1]), dtype=torch.float64, device=dev)
     Y = torch.empty(int(ro[-1]), dtype=torch.float64, device=dev)
-    for b, (nb, mb, rb) in enumerate(shapes):
-        G1, G2, x, e = inputs.factor_stream_factors(nb, mb, rb, noise, inputs.rng_for(workload_id, b))
+    ids = range(len(shapes)) if ids is None else ids
+    for b, ((nb, mb, rb), inst) in enumerate(zip(shapes, ids)):
+        G1, G2, x, e = inputs.factor_stream_factors(nb, mb, rb, noise, inputs.rng_for(workload_id, int(inst)))
         G1t = torch.from_numpy(G1).to(dev)
         G2t = torch.from_numpy(G2).to(dev)
         Ab = G1t @ G2t
@@ -294,11 +296,21 @@ def make_batch_on_gpu(shapes, workload_id, noise, dev):
     return A, Y, torch.from_numpy(ro).to(dev), torch.from_numpy(eo).to(dev), m
 
 
-def run_batched(name, shapes, workload_id, noise, mode, steps, warmup, dev):
+def run_batched(name, shapes, workload_id, noise, mode, steps, warmup, dev, ws=1, rank=0):
+    """Times one batched workload. With several ranks the instances are partitioned by
+    LPT on their cost (each rank keeps the seeded draws of its own instance ids) and the
+    rate is all ranks' rows over the slowest rank's time."""
     import torch
 
+    from paper_2106_11594_gb300 import dist as rgdist
     from paper_2106_11594_gb300 import rg
-    A, Y, ro, eo, m = make_batch_on_gpu(shapes, workload_id, noise, dev)
+    ids = np.arange(len(shapes))
+    if ws > 1:
+        ns, ms_, rs = (np.array([s[i] for s in shapes]) for i in range(3))
+        ids = rgdist.lpt_partition(rgdist.instance_cost(ns, ms_, rs), ws)[rank]
+    all_shapes = shapes
+    shapes = [all_shapes[i] for i in ids]
+    A, Y, ro, eo, m = make_batch_on_gpu(shapes, workload_id, noise, dev, ids)
     bt = rg.RankGrevilleBatch(m, 1e-10, mode)
     X = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
     ranks = torch.empty(len(shapes), dtype=torch.int64, device=dev)
@@ -322,11 +334,13 @@ def run_batched(name, shapes, workload_id, noise, mode, steps, warmup, dev):
     torch.cuda.synchronize()
     bt.sync()
     ms = t0.elapsed_time(t1) / steps
-    rows = int(sum(s[0] for s in shapes))
+    rows_mine = int(sum(s[0] for s in shapes))
     expect = np.array([min(s2) for s2 in shapes])
     rk = ranks.cpu().numpy()
-    out = {"rows_per_s": rows / (ms / 1e3), "ms_per_step": ms, "rows": rows,
-           "instances": len(shapes), "rank_match_generator": int((rk == expect).sum())}
+    rate, ms, rows = rgdist.job_throughput(rows_mine, ms, dev)
+    match = rgdist.sum_over_ranks(float((rk == expect).sum()), dev)
+    out = {"rows_per_s": rate, "ms_per_step": ms, "rows": int(rows),
+           "instances": len(all_shapes), "rank_match_generator": int(match)}
     bt.close()
     del A, Y
     torch.cuda.empty_cache()
@@ -381,6 +395,46 @@ def run_reference(args):
         flush=True)
 
 
+def profile_case(name):
+    """One untimed run of a small case of the hot path, for profilers (ncu -k/-c):
+    stream-k32 / stream-kall (FP64 stream n=4096, m=1024, r=64 in 32-row calls / one
+    call), stream-kall-mixed, batch-uniform-{mixed,fp64} (152 instances of n=2048, m=256,
+    r=32), batch-uneven-mixed (the first 512 shapes of the 4096-instance batch)."""
+    import torch
+
+    from paper_2106_11594_gb300 import inputs, rg
+    dev = torch.device("cuda")
+    if name.startswith("stream"):
+        mode = rg.RG_MIXED if name.endswith("mixed") else rg.RG_FP64
+        k = 32 if name == "stream-k32" else 4096
+        s = inputs.large_stream(4096, M, R)
+        A = torch.from_numpy(s.A).to(dev)
+        Y = torch.from_numpy(s.Y).to(dev)
+        st = rg.RankGreville(M, 1e-10, mode)
+        for j0 in range(0, s.n, k):
+            st.add_rows(A[j0:j0 + k], Y[j0:j0 + k])
+        X = torch.empty(M, dtype=torch.float64, device=dev)
+        print(name, "rank", st.solution(X))
+        st.close()
+        return
+    mode = rg.RG_MIXED if name.endswith("mixed") else rg.RG_FP64
+    if name.startswith("batch-uniform"):
+        shapes, wid, noise = [(2048, 256, 32)] * 152, 4, 1e-3
+    else:
+        n3, m3, r3 = inputs.uneven_batch_shapes()
+        shapes, wid, noise = [(int(a), int(b), int(c)) for a, b, c in zip(n3, m3, r3)][:512], 3, 1e-4
+    A, Y, ro, eo, m = make_batch_on_gpu(shapes, wid, noise, dev)
+    bt = rg.RankGrevilleBatch(m, 1e-10, mode)
+    bt.add_rows(A, ro, eo, Y)
+    X = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+    ranks = torch.empty(len(shapes), dtype=torch.int64, device=dev)
+    bt.solution(X, None, ranks)
+    bt.sync()
+    print(name, "ranks match", int((ranks.cpu().numpy() == np.array([min(x) for x in shapes])).sum()),
+          "of", len(shapes))
+    bt.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -392,8 +446,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--headline-only", action="store_true")
+    ap.add_argument("--profile-case", default=None,
+                    choices=["stream-k32", "stream-kall", "stream-kall-mixed", "batch-uniform-mixed",
+                             "batch-uniform-fp64", "batch-uneven-mixed"],
+                    help="run one small untimed case for a profiler and exit")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        profile_case(args.profile_case)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

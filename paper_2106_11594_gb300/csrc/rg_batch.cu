@@ -96,6 +96,7 @@ __host__ __device__ inline size_t scratch_layout(int kb, int ldm, int rmm, int n
   char* Pp = take((size_t)rmm * rmm * 8);  // one chunk: a CTA team gains nothing from more
   char* up = take((size_t)NCH_MAX * rmm * 8);
   char* Lw = take((size_t)rmm * rmm * 8);
+  char* Kap = take((size_t)SLOW_MAX * SLOW_MAX * 8);
   char* Sp = take((size_t)2 * 32 * 8);  // one worker (the CTA)
   if (S) {
     S->Sp = (double*)Sp;
@@ -105,6 +106,7 @@ __host__ __device__ inline size_t scratch_layout(int kb, int ldm, int rmm, int n
     S->pp_cap = (size_t)rmm * rmm;
     S->up = (double*)up;
     S->Lw = (double*)Lw;
+    S->Kap = (double*)Kap;
     S->G = (double*)G;
     S->spart = (double*)sp;
     S->tpart = (double*)tp;
@@ -120,13 +122,51 @@ __host__ __device__ inline size_t scratch_layout(int kb, int ldm, int rmm, int n
   return off;
 }
 
+// Both modes take TC_SMEM bytes of dynamic shared memory: it holds the rejections of a
+// sequential section when they fit (m <= 256) and, in mixed mode, the operand tiles of the
+// tensor-core projection (never in use at the same time). Mixed mode also sets up the
+// CTA's tensor-core context: one mbarrier and TC_TMEM_COLS columns of tensor memory (at
+// most two CTAs per SM, so the 512 columns of an SM always suffice). FP64 mode runs two
+// CTAs per SM; mixed mode one, with the register budget that its staging needs.
 template <bool MIXED>
-__global__ void __launch_bounds__(NT, 2) batch_kernel(BatchDev D, const double* __restrict__ Gp,
+__global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, const double* __restrict__ Gp,
                                                    const int64_t* __restrict__ roff,
                                                    const int64_t* __restrict__ eoff,
                                                    const double* __restrict__ yp, uint8_t* indep) {
   __shared__ int item;
+  __shared__ TcCtx tcx;
+  __shared__ __align__(8) unsigned long long tc_bar;
+  __shared__ uint32_t tc_tmem;
+  extern __shared__ __align__(1024) unsigned char dyn_smem[];
+  float* const dyn_base = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~static_cast<uintptr_t>(1023));
+  if (MIXED) {
+    if (threadIdx.x < 32) {  // warp 0 owns the allocation
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tc_tmem)),
+                   "r"(TC_TMEM_COLS));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tc_bar)));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      float* base = dyn_base;
+      tcx.Ahi = base;
+      tcx.Alo = base + TC_TILE;
+      tcx.Bhi = base + 2 * TC_TILE;
+      tcx.Blo = base + 3 * TC_TILE;
+      tcx.bar = &tc_bar;
+      tcx.phase = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0) tcx.tmem = tc_tmem;
+    __syncthreads();
+  }
   StreamDev S{};
+  S.tcx = MIXED ? (void*)&tcx : nullptr;
+  S.Rs = reinterpret_cast<double*>(dyn_base);
+  S.rs_cap = (TC_SMEM - 1024) / 8;
   S.mixed = MIXED;
   S.test_mode = D.test_mode;
   S.tol = D.tol;
@@ -159,12 +199,20 @@ __global__ void __launch_bounds__(NT, 2) batch_kernel(BatchDev D, const double* 
     S.ctrl = D.ctrl + (size_t)b * CTRL_N;
     S.rows_seen = D.rows_seen + b;
     CallArgs A{Gp + eoff[b], yp + roff[b], n, indep ? indep + roff[b] : nullptr};
-    process_rows<CtaTeam, MIXED>(CtaTeam{}, S, A);
+    const bool ok = process_rows<CtaTeam, MIXED>(CtaTeam{}, S, A);
     __syncthreads();
     if (threadIdx.x == 0) {
       const int st = ld_acquire_i32(S.ctrl + CTRL_STATUS);
       if (st) atomicOr(D.bstatus, st);
     }
+    if (!ok) break;  // a bounded wait gave up: stop taking work
+  }
+  if (MIXED) {
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x < 32)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tcx.tmem), "r"(TC_TMEM_COLS));
   }
 }
 
@@ -324,12 +372,19 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
   int nsm = 0, per = 0;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, bt->device);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(D.mixed ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  if (e == cudaSuccess)  // up to two CTAs of ~105 KiB each per SM
+    e = cudaFuncSetAttribute(D.mixed ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per, D.mixed ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>, NT, 0);
+        &per, D.mixed ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>, NT, TC_SMEM);
   if (e != cudaSuccess || per <= 0) {
     delete bt;
     return e != cudaSuccess ? cuda_fail(e, "rg_batch_init: occupancy") : fail(RG_ECUDA, "rg_batch_init: no occupancy");
   }
+  per = std::min(per, 2);  // tensor memory: TC_TMEM_COLS per CTA, 512 columns per SM
   bt->grid = std::min<long long>((long long)nsm * per, B);
   // host-side layout
   std::vector<long long> soff(B), xoff(B + 1, 0);
@@ -407,10 +462,10 @@ rg_status rg_batch_add_rows(rg_batch* bt, const double* Gamma_packed, const int6
     // kernel writes every applied row and the rest are left as the caller initialised them
   }
   if (D.mixed)
-    batch_kernel<true><<<bt->grid, NT, 0, bt->stream>>>(D, Gamma_packed, row_offsets, elem_offsets,
+    batch_kernel<true><<<bt->grid, NT, TC_SMEM, bt->stream>>>(D, Gamma_packed, row_offsets, elem_offsets,
                                                         y_packed, indep_out);
   else
-    batch_kernel<false><<<bt->grid, NT, 0, bt->stream>>>(D, Gamma_packed, row_offsets, elem_offsets,
+    batch_kernel<false><<<bt->grid, NT, TC_SMEM, bt->stream>>>(D, Gamma_packed, row_offsets, elem_offsets,
                                                          y_packed, indep_out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "rg_batch_add_rows: launch");

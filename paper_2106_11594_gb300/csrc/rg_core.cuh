@@ -29,6 +29,7 @@
 #include <type_traits>
 
 #include "rg_internal.cuh"
+#include "rg_tc.cuh"
 
 namespace rg {
 
@@ -222,8 +223,10 @@ __device__ void phase_gamma(const Team& T, const StreamDev& S, const double* __r
 // ..., so each staged basis tile serves 4 RPT rows. The basis tile (RC ranks x MC
 // columns) and the gamma slice are staged in shared memory per chunk of RC ranks. RPT = 1
 // spreads small blocks over many CTAs; RPT = 8 is used for large blocks. Writes per-chunk
-// partial sums of ||Gamma_r||^2 and ||Gamma||^2 (FP64) and, when Rout != null, the FP64
-// rejections (row j at Rout[(j - row_lo) * ld]).
+// partial sums of ||Gamma_r||^2 and ||Gamma||^2 and, when Rout != null, the FP64
+// rejections (row j at Rout[(j - row_lo) * ld]). The partial sums are FP64 in FP64 mode;
+// in the FP32 screen of mixed mode they are FP32 sums over the MC columns of a chunk (the
+// screen only compares s against tau_lo^2 t, and FP64 arithmetic is 1/64 of FP32 here).
 template <class Team, bool F32, int RPT>
 __device__ void phase_reject(const Team& T, const StreamDev& S, const double* __restrict__ gam,
                              int row_lo, int row_hi, int r, const double* __restrict__ back64,
@@ -289,31 +292,37 @@ __device__ void phase_reject(const Team& T, const StreamDev& S, const double* __
         for (int q = 0; q < RPT; ++q) acc[q][0] = fma(-b0, Gs[(rl + 4 * q) * RC + ii], acc[q][0]);
       }
     }
-    double sv[RPT], tv[RPT];
+    V sv[RPT], tv[RPT];
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
       const int j = jb + rl + 4 * q;
       const bool valid = (j < row_hi && c < m);
       const V a = acc[q][0] + acc[q][1];
-      sv[q] = valid ? (double)a * (double)a : 0.0;
-      tv[q] = valid ? gv[q] * gv[q] : 0.0;
+      const V g = (V)gv[q];
+      sv[q] = valid ? a * a : V(0);
+      tv[q] = valid ? g * g : V(0);
       if (!F32 && Rout && valid) Rout[(size_t)(j - row_lo) * ld + c] = (double)a;
     }
     // per warp: the 32 columns of its row lane; lanes reduce the RPT rows at once
-    double ts, tt;
+    V ts, tt;
     int qi = 0;
     if (RPT == 1) {
-      ts = warp_sum(sv[0]);
-      tt = warp_sum(tv[0]);
+      ts = sv[0];
+      tt = tv[0];
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) {
+        ts += __shfl_xor_sync(0xffffffffu, ts, off);
+        tt += __shfl_xor_sync(0xffffffffu, tt, off);
+      }
     } else {
-      ts = warp_transpose_sum<double, RPT>(sv);
-      tt = warp_transpose_sum<double, RPT>(tv);
+      ts = warp_transpose_sum<V, RPT>(sv);
+      tt = warp_transpose_sum<V, RPT>(tv);
       qi = transpose_sum_index<RPT>();
     }
     __syncthreads();
     if ((lane & (32 / RPT - 1)) == 0) {
-      red_s[warp][qi] = ts;
-      red_t[warp][qi] = tt;
+      red_s[warp][qi] = (double)ts;
+      red_t[warp][qi] = (double)tt;
     }
     __syncthreads();
     if (threadIdx.x < RB) {  // row a = rl + 4 q: warps 2 rl and 2 rl + 1 hold its columns
@@ -382,6 +391,13 @@ __device__ void phase_dall(const Team& T, const StreamDev& S, const CallArgs& A,
   }
 }
 
+// FP32 screen of mixed mode: true if the row is certainly dependent (relative rejection
+// at most tc). Rows whose squared norm leaves the range where FP32 squares and sums are
+// exact enough (including zero rows) are not screened: the FP64 section decides them.
+__device__ __forceinline__ bool fp32_screen_dependent(double s, double t, double tc) {
+  return t > 1e-30 && t < 1e30 && s <= tc * tc * t;
+}
+
 // Reduce the partial norms of rows [0, b), decide every row and return the first row that
 // needs the sequential section (independent, FP32 candidate, or non-finite). Every CTA that
 // calls it gets the same answer (same data, same summation order); with `publish` the CTA
@@ -424,7 +440,7 @@ __device__ int decide_rows(const StreamDev& S, const CallArgs& A, long long j0, 
         const double yv = __ldg(A.y + j0 + j);
         bool special = !isfinite(t) || !isfinite(yv);
         if (!special) {
-          if (MIXED) special = s > tc * tc * t;
+          if (MIXED) special = !fp32_screen_dependent(s, t, tc);
           else special = is_independent(s, t, r, S.m, S.tol, S.test_mode);
         }
         if (special) atomicMin(&q0, j);
@@ -463,7 +479,7 @@ __device__ void decide_rows_team(const Team& T, const StreamDev& S, const CallAr
       const double yv = __ldg(A.y + j0 + j);
       bool special = !isfinite(t) || !isfinite(yv);
       if (!special) {
-        if (MIXED) special = s > tc * tc * t;
+        if (MIXED) special = !fp32_screen_dependent(s, t, tc);
         else special = is_independent(s, t, r, S.m, S.tol, S.test_mode);
       }
       if (special) atomicMin(S.ctrl + CTRL_Q0, (int)j);
@@ -479,20 +495,22 @@ __device__ void decide_rows_team(const Team& T, const StreamDev& S, const CallAr
 // up to EMAX entries per thread per pass; the gamma rows of the run (and their D) are
 // staged in shared memory in row chunks. Ranks whose gamma rows do not fit the pool read
 // G from L2 directly.
-template <class Team>
+template <class Team, bool F32>
 __device__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int r) {
+  using V = typename std::conditional<F32, float, double>::type;
   const int rm = S.r_max;
   const long long tstride = (long long)T.size() * NT;
   const long long nP = (long long)r * r, ntot = nP + r;
   constexpr int EMAX = 4;
-  const bool staged = (r + 1) <= (POOL_DOUBLES - 64);
-  double* Gs = smem_pool();
-  const int rows_per = staged ? max(1, min(len, (POOL_DOUBLES - 64) / (r + 1))) : 1;
-  double* Ds = Gs + (size_t)rows_per * r;
+  constexpr int POOL_V = POOL_DOUBLES * (int)(sizeof(double) / sizeof(V));
+  const bool staged = (r + 1) <= (POOL_V - 64);
+  V* Gs = reinterpret_cast<V*>(smem_pool());
+  const int rows_per = staged ? max(1, min(len, (POOL_V - 64) / (r + 1))) : 1;
+  V* Ds = Gs + (size_t)rows_per * r;
   for (long long base = 0; base < ntot; base += (long long)EMAX * tstride) {
-    double acc[EMAX];
+    V acc[EMAX];
 #pragma unroll
-    for (int q = 0; q < EMAX; ++q) acc[q] = 0.0;
+    for (int q = 0; q < EMAX; ++q) acc[q] = V(0);
     const long long e0 = base + rr_thread(T);
     for (int jb = a; jb < a + len; jb += rows_per) {
       const int nr = min(rows_per, a + len - jb);
@@ -501,9 +519,9 @@ __device__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int
 #pragma unroll 8
         for (int e = threadIdx.x; e < nr * r; e += NT) {
           const int jj = e / r, i = e - jj * r;
-          Gs[e] = __ldcg(S.G + (size_t)(jb + jj) * rm + i);
+          Gs[e] = (V)__ldcg(S.G + (size_t)(jb + jj) * rm + i);
         }
-        for (int e = threadIdx.x; e < nr; e += NT) Ds[e] = __ldcg(S.Dall + jb + e);
+        for (int e = threadIdx.x; e < nr; e += NT) Ds[e] = (V)__ldcg(S.Dall + jb + e);
         __syncthreads();
       }
 #pragma unroll
@@ -513,15 +531,15 @@ __device__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int
         const bool isP = e < nP;
         const int i = isP ? (int)(e / r) : (int)(e - nP);
         const int l = isP ? (int)(e - (long long)i * r) : 0;
-        double x0 = 0.0, x1 = 0.0;
+        V x0 = V(0), x1 = V(0);
         for (int jj = 0; jj < nr; ++jj) {
-          double gi, gl;
+          V gi, gl;
           if (staged) {
             gi = Gs[jj * r + i];
             gl = isP ? Gs[jj * r + l] : Ds[jj];
           } else {
-            gi = __ldcg(S.G + (size_t)(jb + jj) * rm + i);
-            gl = isP ? __ldcg(S.G + (size_t)(jb + jj) * rm + l) : __ldcg(S.Dall + jb + jj);
+            gi = (V)__ldcg(S.G + (size_t)(jb + jj) * rm + i);
+            gl = (V)(isP ? __ldcg(S.G + (size_t)(jb + jj) * rm + l) : __ldcg(S.Dall + jb + jj));
           }
           if (jj & 1) x1 = fma(gi, gl, x1);
           else x0 = fma(gi, gl, x0);
@@ -536,10 +554,10 @@ __device__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int
       if (e < nP) {
         const int i = (int)(e / r), l = (int)(e - (long long)i * r);
         const size_t o = (size_t)i * rm + l;
-        S.P[o] = __ldcg(S.P + o) + acc[q];
+        S.P[o] = __ldcg(S.P + o) + (double)acc[q];
       } else {
         const int i = (int)(e - nP);
-        S.u[i] = __ldcg(S.u + i) + acc[q];
+        S.u[i] = __ldcg(S.u + i) + (double)acc[q];
       }
     }
   }
@@ -547,11 +565,12 @@ __device__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int
 
 // Long runs, step 1: partial Gram sums per chunk of rows; CTA item = (16 x 16 tile pair
 // with ti <= tl, chunk). Diagonal tiles also accumulate sum_j gamma_j D_j for their rows.
-template <class Team>
+template <class Team, bool F32>
 __device__ void gram_partials(const Team& T, const StreamDev& S, int a, int len, int r, int nch) {
-  double(*gi_s)[17] = reinterpret_cast<double(*)[17]>(smem_pool());
-  double(*gl_s)[17] = gi_s + 32;
-  double* d_s = reinterpret_cast<double*>(gl_s + 32);
+  using V = typename std::conditional<F32, float, double>::type;
+  V(*gi_s)[17] = reinterpret_cast<V(*)[17]>(smem_pool());
+  V(*gl_s)[17] = gi_s + 32;
+  V* d_s = reinterpret_cast<V*>(gl_s + 32);
   const int rm = S.r_max;
   const int nt = (r + 15) / 16;
   const int npairs = nt * (nt + 1) / 2;
@@ -566,17 +585,17 @@ __device__ void gram_partials(const Team& T, const StreamDev& S, int a, int len,
     }
     const int tl = ti + pr;
     const int jlo = a + c * per, jhi = min(a + len, jlo + per);
-    double acc = 0.0, uacc = 0.0;
+    V acc = V(0), uacc = V(0);
     for (int jb = jlo; jb < jhi; jb += 32) {
       __syncthreads();
 #pragma unroll 2
       for (int e = threadIdx.x; e < 32 * 16; e += NT) {
         const int jj = e >> 4, cc = e & 15;
         const int j = jb + jj, i = ti * 16 + cc, l = tl * 16 + cc;
-        gi_s[jj][cc] = (j < jhi && i < r) ? __ldcg(S.G + (size_t)j * rm + i) : 0.0;
-        gl_s[jj][cc] = (j < jhi && l < r) ? __ldcg(S.G + (size_t)j * rm + l) : 0.0;
+        gi_s[jj][cc] = (j < jhi && i < r) ? (V)__ldcg(S.G + (size_t)j * rm + i) : V(0);
+        gl_s[jj][cc] = (j < jhi && l < r) ? (V)__ldcg(S.G + (size_t)j * rm + l) : V(0);
       }
-      if (threadIdx.x < 32) d_s[threadIdx.x] = (jb + threadIdx.x < jhi) ? __ldcg(S.Dall + jb + threadIdx.x) : 0.0;
+      if (threadIdx.x < 32) d_s[threadIdx.x] = (jb + threadIdx.x < jhi) ? (V)__ldcg(S.Dall + jb + threadIdx.x) : V(0);
       __syncthreads();
 #pragma unroll 8
       for (int jj = 0; jj < 32; ++jj) {
@@ -586,8 +605,8 @@ __device__ void gram_partials(const Team& T, const StreamDev& S, int a, int len,
     }
     const int i = ti * 16 + ty, l = tl * 16 + tx;
     double* Pc = S.Pp + (size_t)c * r * r;
-    if (i < r && l < r) Pc[(size_t)i * r + l] = acc;
-    if (ti == tl && tx == 0 && i < r) S.up[(size_t)c * rm + i] = uacc;
+    if (i < r && l < r) Pc[(size_t)i * r + l] = (double)acc;
+    if (ti == tl && tx == 0 && i < r) S.up[(size_t)c * rm + i] = (double)uacc;
   }
 }
 
@@ -617,153 +636,298 @@ __device__ void gram_reduce(const Team& T, const StreamDev& S, int r, int nch) {
 
 // A run of dependent rows [a, a + len): short runs directly, long runs through chunked
 // partial sums. Returns false if a team barrier gave up. The caller syncs afterwards.
-template <class Team>
+// F32 (mixed mode): the per-chunk sums of gamma gamma^T and gamma D are FP32 (the gammas
+// are FP32 projections), added to the FP64 P and u.
+template <class Team, bool F32>
 __device__ bool dep_run(const Team& T, const StreamDev& S, int a, int len, int r) {
   if (len <= 0 || r == 0) return true;
   const size_t rr = (size_t)r * r;
   if (len > SMALL_B && S.Pp && S.pp_cap >= rr) {
     int nch = (int)min((size_t)NCH_MAX, S.pp_cap / rr);
     nch = max(1, min(nch, (len + GRAM_CHUNK - 1) / GRAM_CHUNK));
-    gram_partials(T, S, a, len, r, nch);
+    gram_partials<Team, F32>(T, S, a, len, r, nch);
     if (!T.sync()) return false;
     gram_reduce(T, S, r, nch);
     return true;
   }
-  acc_small(T, S, a, len, r);
+  acc_small<Team, F32>(T, S, a, len, r);
   return true;
 }
 
 // =======================================================================================
-// Sequential section, team-wide: rows [q0, bend) with FP64 G and R (R row j at
-// S.R[(j - q0) * ld]). Rows are decided in order; after each append the later rows of the
-// section are fixed up (their rejections lose the new direction:
-// Gamma_r,t -= kappa_t Gamma_r,j, kappa_t = K_j^T Gamma_r,t). Every worker owns a slice of
-// the columns; per row one pass computes the partial ||Gamma_r,j||^2 and the partial dot
-// products with all later rows of the section, the partials are exchanged through S.Sp
-// (double-buffered by row parity) across one team barrier and summed by every worker in
-// the same order, so all workers take the same decision. S.Sp holds, per parity,
-// 32 partials for each of the first min(workers, ceil(m / NT)) workers. Worker 0 keeps the bookkeeping:
-// the data of each append, w_b, the rank-row record, the flags and, for every applied row,
-// its a-priori error against w_b as it stands when the row is reached.
-// Returns false if a barrier gave up; out = {applied, r_new, n_ind}.
+// Sequential section: rows [q0, bend) (at most SLOW_MAX) with FP64 coordinates in S.G and
+// FP64 rejections in S.R (row j at S.R[(j - q0) * ld]). Rows are decided in order; after
+// an append the later rejections of the section lose the new direction
+// (Gamma_r,t -= kappa_t Gamma_r,j with kappa_t = Gamma_r,j^T Gamma_r,t / s_j, modified
+// Gram-Schmidt, valid because Gamma_r,j is orthogonal to span(C)).
+//
+// The columns are split over the first nact = min(workers, ceil(m / NT)) workers. Per row
+// every column owner forms its part of s_j = ||Gamma_r,j||^2 and of the dot products with
+// the later rows, the parts are summed (across the warps of a CTA in shared memory; across
+// CTAs through S.Sp, double-buffered by row parity, after a barrier over the nact workers
+// only, always in the same order), and every owner takes the same decision. Each thread
+// keeps its column of the section's rejections in registers when it owns one column
+// (REG), otherwise they stay in shared memory (S.Rs, when they fit) or in S.R.
+// Only decisions, kappa_t, the new basis rows K and the append records are produced in the
+// row loop; worker 0 then replays the appends on the coordinates of the section's rows
+// (gamma_t <- [gamma_t - kappa_t gamma_j; kappa_t], orthonormal: [gamma_t; kappa_t sqrt(s_j)])
+// in one pass in which every thread owns one coordinate, and forms the a-priori errors
+// D_t = y_t - gamma_t^T w_b with w_b as it stands when row t is reached.
+// Publishes {applied, r_new, n_ind} in CTRL_APPLIED / CTRL_RNEW / CTRL_NIND; the caller
+// reads them after its next team barrier. Returns false if a bounded wait gave up.
 // =======================================================================================
-template <class Team, bool ORTHO>
-__device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, long long j0, int q0,
-                          int bend, int r, int out[3]) {
-  const int m = S.m, ld = S.ld, rm = S.r_max;
-  const long long col0 = (long long)T.id() * NT + threadIdx.x;
-  const long long cstride = (long long)T.size() * NT;
-  __shared__ double tot[32];
-  __shared__ double wred[NWARP][32];
-  __shared__ int dec_s;
-  __shared__ double dv_s;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // workers that own columns (the column slices are NT wide); only they publish partials
-  const int nact = (int)min((long long)T.size(), ((long long)m + NT - 1) / NT);
-  int rc = r, nind = 0, applied = bend;
-  const long long base_row = __ldcg(S.rows_seen);
-  for (int j = q0; j < bend; ++j) {
-    const int nt = bend - j - 1;
-    const double* Rj = S.R + (size_t)(j - q0) * ld;
-    // partials over my columns: v[0] = ||R_j||^2, v[1 + t] = R_j . R_{j+1+t}
-    double v[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) v[q] = 0.0;
-    for (long long c = col0; c < m; c += cstride) {
-      const double rj = __ldcg(Rj + c);
-      v[0] = fma(rj, rj, v[0]);
-#pragma unroll
-      for (int t = 0; t < 31; ++t)
-        if (t < nt) v[1 + t] = fma(rj, __ldcg(S.R + (size_t)(j + 1 + t - q0) * ld + c), v[1 + t]);
-    }
-    warp_transpose_sum32(v);  // lane l holds the warp's sum of value l
-    wred[warp][lane] = v[0];
-    __syncthreads();
-    double* Sp = S.Sp + (size_t)(j & 1) * S.sp_stride;
-    if (T.id() < nact && threadIdx.x < 32) {
-      double a = 0.0;
-#pragma unroll
-      for (int w2 = 0; w2 < NWARP; ++w2) a += wred[w2][threadIdx.x];
-      Sp[(size_t)T.id() * 32 + threadIdx.x] = a;
-    }
-    // worker 0: the a-priori error of row j against the current w_b
-    double dp = 0.0;
-    if (T.id() == 0) {
-      const double* gj = S.G + (size_t)j * rm;
-      for (int i = threadIdx.x; i < rc; i += NT) dp = fma(__ldcg(gj + i), __ldcg(S.wb + i), dp);
-      dp = block_sum(dp);
-      if (threadIdx.x == 0) dv_s = __ldg(A.y + j0 + j) - dp;
-    }
-    if (!T.sync()) return false;
-    // every worker sums the partials in the same order
-    if (threadIdx.x < 32) {
-      double a = 0.0;
-      for (int w2 = 0; w2 < nact; ++w2) a += __ldcg(Sp + (size_t)w2 * 32 + threadIdx.x);
-      tot[threadIdx.x] = a;
-    }
-    __syncthreads();
-    const double s = tot[0];
-    const double t = __ldcg(S.t + j);
-    const double yv = __ldg(A.y + j0 + j);
-    if (threadIdx.x == 0) {
-      int d = 0;
-      if (!isfinite(t) || !isfinite(yv) || !isfinite(s)) d = -1;
-      else if (is_independent(s, t, rc, m, S.tol, S.test_mode)) d = (rc >= rm) ? -2 : 1;
-      dec_s = d;
-    }
-    __syncthreads();
-    const int d = dec_s;
-    if (d < 0) {
-      if (T.id() == 0 && threadIdx.x == 0)
-        atomicOr(S.ctrl + CTRL_STATUS, d == -1 ? ST_NONFINITE : ST_CAPACITY);
-      applied = j;
-      break;
-    }
-    if (T.id() == 0 && threadIdx.x == 0) {
-      S.rowflag[j] = (uint8_t)(d + 1);
-      S.Dall[j] = dv_s;
-    }
-    if (d == 1) {  // independent: record the append, fix up the later rows
-      const int q = nind;
-      const double scale = ORTHO ? 1.0 / sqrt(s) : 1.0 / s;
-      const double is = 1.0 / s, sq = sqrt(s);
-      double* Kq = S.Kv + (size_t)q * ld;
-      for (long long c = col0; c < m; c += cstride) {
-        const double rj = __ldcg(Rj + c);
-        Kq[c] = rj * scale;
-#pragma unroll
-        for (int tt = 0; tt < 31; ++tt)
-          if (tt < nt) {
-            double* Rt = S.R + (size_t)(j + 1 + tt - q0) * ld;
-            Rt[c] = fma(-tot[1 + tt] * is, rj, __ldcg(Rt + c));
-          }
-      }
-      if (T.id() == 0) {
-        const double* gj = S.G + (size_t)j * rm;
-        for (int i = threadIdx.x; i < rc; i += NT) S.Gind[(size_t)q * rm + i] = __ldcg(gj + i);
-        if (threadIdx.x == 0) {
-          S.jind[q] = j;
-          S.alpha[q] = 1.0 / sq;
-          S.basis_rows[rc] = base_row + j;
-          S.wb[rc] = ORTHO ? 0.0 : yv;  // w_b <- [w_b; y] (general) or [w_b; 0] (orthonormal)
+__device__ __forceinline__ bool sub_barrier(int* ctrl, int n, unsigned long long& target) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ctrl + CTRL_SUB_COUNT);
+    target += (unsigned long long)n;
+    red_release_add_u64(cnt, 1ull);
+    if (ld_acquire_u64(cnt) < target) {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire_u64(cnt) < target) {
+        if (global_ns() - t0 > WAIT_LIMIT_NS) {
+          atomicOr(ctrl + CTRL_STATUS, ST_TIMEOUT);
+          ok = 0;
+          break;
         }
-        // coordinates of the later rows gain the new direction
-        for (int e = threadIdx.x; e < nt * (rc + 1); e += NT) {
-          const int tt = e / (rc + 1), i = e - tt * (rc + 1);
-          double* gt = S.G + (size_t)(j + 1 + tt) * rm;
-          const double kap = tot[1 + tt] * is;
-          if (i == rc) gt[rc] = ORTHO ? kap * sq : kap;
-          else if (!ORTHO) gt[i] = fma(-kap, __ldcg(gj + i), __ldcg(gt + i));
-        }
-        __syncthreads();
       }
-      ++rc;
-      ++nind;
     }
   }
-  out[0] = applied;
-  out[1] = rc;
-  out[2] = nind;
+  __syncthreads();
+  return ok != 0;
+}
+
+// Sums this worker's 32 partials (one set per thread) over the CTA and over the nact
+// column owners; the result lands in tot[0..31] for every thread of every owner.
+template <class Team>
+__device__ __forceinline__ bool scan_exchange(const Team& T, const StreamDev& S, double (&v)[32], int nact,
+                                              int parity, unsigned long long& bar_target, double* tot,
+                                              double (*wred)[32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_transpose_sum32(v);  // lane l holds the warp's sum of value l
+  wred[warp][lane] = v[0];
+  __syncthreads();
+  double a = 0.0;
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int w2 = 0; w2 < NWARP; ++w2) a += wred[w2][threadIdx.x];
+  }
+  if (nact > 1) {
+    double* Sp = S.Sp + (size_t)parity * S.sp_stride;
+    if (threadIdx.x < 32) Sp[(size_t)T.id() * 32 + threadIdx.x] = a;
+    if (!sub_barrier(S.ctrl, nact, bar_target)) return false;
+    if (threadIdx.x < 32) {
+      a = 0.0;
+      for (int w2 = 0; w2 < nact; ++w2) a += __ldcg(Sp + (size_t)w2 * 32 + threadIdx.x);
+    }
+  }
+  if (threadIdx.x < 32) tot[threadIdx.x] = a;
+  __syncthreads();
+  return true;
+}
+
+template <class Team, bool ORTHO>
+__device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, long long j0, int q0,
+                          int bend, int r) {
+  const int m = S.m, ld = S.ld, rm = S.r_max;
+  const int nrow = bend - q0;
+  const int nact = (int)min((long long)T.size(), ((long long)m + NT - 1) / NT);
+  __shared__ double tot[32];
+  __shared__ double wred[NWARP][32];
+  __shared__ double ts[32], ys[32], ss[32];
+  __shared__ int flag_s[32];
+  __shared__ int dec_s;
+  const int tid = threadIdx.x;
+  int rc = r, nind = 0, applied = bend;
+  if (T.id() < nact) {
+    const long long base_row = __ldcg(S.rows_seen);
+    if (tid < 32) {
+      ts[tid] = (tid < nrow) ? __ldcg(S.t + q0 + tid) : 0.0;
+      ys[tid] = (tid < nrow) ? __ldg(A.y + j0 + q0 + tid) : 0.0;
+      flag_s[tid] = 0;
+    }
+    __shared__ unsigned long long bar_target_s;
+    if (tid == 0 && nact > 1) {
+      const unsigned long long c = ld_acquire_u64(reinterpret_cast<unsigned long long*>(S.ctrl + CTRL_SUB_COUNT));
+      bar_target_s = (c / (unsigned long long)nact) * (unsigned long long)nact;
+    }
+    __syncthreads();
+    unsigned long long bar_target = bar_target_s;
+    // grid teams with one column per thread keep the rejections in registers
+    const long long cstride = (long long)nact * NT;
+    constexpr bool kGrid = std::is_same<Team, GridTeam>::value;
+    // decision of row jj (thread 0), records (worker 0), kappa of the later rows
+    auto decide = [&](int jj) -> int {
+      const int j = q0 + jj;
+      if (tid == 0) {
+        const double s = tot[0], t = ts[jj], yv = ys[jj];
+        int d = 0;
+        if (!isfinite(t) || !isfinite(yv) || !isfinite(s)) d = -1;
+        else if (is_independent(s, t, rc, m, S.tol, S.test_mode)) d = (rc >= rm) ? -2 : 1;
+        if (T.id() == 0) {
+          if (d < 0) {
+            atomicOr(S.ctrl + CTRL_STATUS, d == -1 ? ST_NONFINITE : ST_CAPACITY);
+          } else {
+            flag_s[jj] = d + 1;
+            S.rowflag[j] = (uint8_t)(d + 1);
+            ss[jj] = s;
+            if (d == 1) {
+              S.jind[nind] = j;
+              S.alpha[nind] = 1.0 / sqrt(s);
+              S.basis_rows[rc] = base_row + j;
+              S.wb[rc] = ORTHO ? 0.0 : yv;  // w_b <- [w_b; y] (general) or [w_b; 0] (orthonormal)
+            }
+          }
+        }
+        dec_s = d;
+      }
+      __syncthreads();
+      const int d = dec_s;
+      if (d == 1 && T.id() == 0 && tid >= 1 && tid < 32 && jj + tid < nrow)
+        S.Kap[nind * SLOW_MAX + jj + tid] = tot[tid] / tot[0];
+      return d;
+    };
+    bool done = false;
+    if constexpr (kGrid) {
+      if ((long long)m <= cstride) {
+      done = true;
+      const long long c = (long long)T.id() * NT + tid;
+      const bool cv = c < m;
+      double R[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) R[k] = (cv && k < nrow) ? __ldcg(S.R + (size_t)k * ld + c) : 0.0;
+      for (int jj = 0; jj < nrow; ++jj) {
+        double v[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = R[0] * R[k];
+        if (!scan_exchange(T, S, v, nact, jj & 1, bar_target, tot, wred)) return false;
+        const int d = decide(jj);
+        if (d < 0) {
+          applied = q0 + jj;
+          break;
+        }
+        if (d == 1) {
+          const double s = tot[0], is = 1.0 / s;
+          const double scale = ORTHO ? 1.0 / sqrt(s) : is;
+          if (cv) S.Kv[(size_t)nind * ld + c] = R[0] * scale;
+#pragma unroll
+          for (int k = 1; k < 32; ++k) R[k] = fma(-tot[k] * is, R[0], R[k]);
+          ++rc;
+          ++nind;
+        }
+#pragma unroll
+        for (int k = 0; k < 31; ++k) R[k] = R[k + 1];
+        R[31] = 0.0;
+      }
+      }
+    }
+    if (!done) {
+      // rejections in shared memory (row stride m) when they fit, else in S.R (global,
+      // read through L2 since other CTAs wrote it); `rsm` selects plain shared-memory loads
+      double* Rb = S.R;
+      long long ldr = ld;
+      bool rsm = false;
+      if (nact == 1 && S.Rs && (long long)nrow * m <= S.rs_cap) {
+        for (long long e = tid; e < (long long)nrow * m; e += NT) {
+          const long long k = e / m, c = e - k * m;
+          S.Rs[e] = __ldcg(S.R + (size_t)k * ld + c);
+        }
+        __syncthreads();
+        Rb = S.Rs;
+        ldr = m;
+        rsm = true;
+      }
+      auto rload = [&](const double* p) -> double { return rsm ? *p : __ldcg(p); };
+      const long long col0 = (long long)T.id() * NT + tid;
+      for (int jj = 0; jj < nrow; ++jj) {
+        double v[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = 0.0;
+        for (long long c = col0; c < m; c += cstride) {
+          const double rj = rload(Rb + (size_t)jj * ldr + c);
+#pragma unroll
+          for (int k = 0; k < 32; ++k)
+            if (jj + k < nrow) v[k] = fma(rj, rload(Rb + (size_t)(jj + k) * ldr + c), v[k]);
+        }
+        if (!scan_exchange(T, S, v, nact, jj & 1, bar_target, tot, wred)) return false;
+        const int d = decide(jj);
+        if (d < 0) {
+          applied = q0 + jj;
+          break;
+        }
+        if (d == 1) {
+          const double s = tot[0], is = 1.0 / s;
+          const double scale = ORTHO ? 1.0 / sqrt(s) : is;
+          for (long long c = col0; c < m; c += cstride) {
+            const double rj = rload(Rb + (size_t)jj * ldr + c);
+            S.Kv[(size_t)nind * ld + c] = rj * scale;
+#pragma unroll
+            for (int k = 1; k < 32; ++k)
+              if (jj + k < nrow) {
+                double* rt = Rb + (size_t)(jj + k) * ldr + c;
+                *rt = fma(-tot[k] * is, rj, rload(rt));
+              }
+          }
+          ++rc;
+          ++nind;
+        }
+      }
+    }
+  }
+  if (T.id() == 0) {
+    // replay the appends on the coordinates: thread = coordinate i (of the final rank rc)
+    const int napp = applied - q0;
+    __syncthreads();
+    for (int i0 = 0; i0 < rc; i0 += NT) {
+      const int i = i0 + tid;
+      double g[32];
+#pragma unroll
+      for (int tt = 0; tt < 32; ++tt) g[tt] = (tt < napp && i < r) ? __ldcg(S.G + (size_t)(q0 + tt) * rm + i) : 0.0;
+      int rcv = r, q = 0;
+#pragma unroll
+      for (int tt = 0; tt < 32; ++tt) {
+        if (tt < napp) {
+          if (i < rcv) S.G[(size_t)(q0 + tt) * rm + i] = g[tt];
+          if (flag_s[tt] == 2) {
+            if (i < rcv) S.Gind[(size_t)q * rm + i] = g[tt];
+            const double sq = sqrt(ss[tt]);
+#pragma unroll
+            for (int t2 = tt + 1; t2 < 32; ++t2) {
+              if (t2 < napp) {
+                const double kap = __ldcg(S.Kap + q * SLOW_MAX + t2);
+                if (i < rcv) {
+                  if (!ORTHO) g[t2] = fma(-kap, g[tt], g[t2]);
+                } else if (i == rcv) {
+                  g[t2] = ORTHO ? kap * sq : kap;
+                }
+              }
+            }
+            ++rcv;
+            ++q;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // a-priori errors: one warp per row, w_b entries below the rank the row saw
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int tt = warp; tt < napp; tt += NWARP) {
+      int rk = r;
+      for (int u2 = 0; u2 < tt; ++u2) rk += (flag_s[u2] == 2);
+      const double* g = S.G + (size_t)(q0 + tt) * rm;
+      double acc = 0.0;
+      for (int l = lane; l < rk; l += 32) acc = fma(__ldcg(g + l), __ldcg(S.wb + l), acc);
+      acc = warp_sum(acc);
+      if (lane == 0) S.Dall[q0 + tt] = ys[tt] - acc;
+    }
+    if (tid == 0) {
+      S.ctrl[CTRL_APPLIED] = applied;
+      S.ctrl[CTRL_RNEW] = rc;
+      S.ctrl[CTRL_NIND] = nind;
+    }
+  }
   return true;
 }
 
@@ -889,49 +1053,63 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
     const bool last = (j0 + b == A.k);
     const double* gam = A.Gamma + (size_t)j0 * S.m;
     __syncthreads();
-    // 1: gamma of every row against the block-start basis
-    if (T.id() == 0 && threadIdx.x == 0) S.ctrl[CTRL_Q0] = b;
-    // larger items only while they still give every worker at least two
-    const bool big_rej = (long long)(b / 32) * S.nmc >= 2LL * T.size();
-    const int gr = min(8, (int)((POOL_DOUBLES * 2) / max(S.m, 1)));  // FP32 rows that fit
-    if (MIXED && gr >= 1 && (long long)(b / gr) >= 2LL * T.size())
-      phase_gamma_f32_staged(T, S, gam, 0, b, r, gr);
-    else
-      phase_gamma<Team, MIXED>(T, S, gam, 0, b, r, MIXED ? S.C : S.Ct);
-    if (!T.sync()) return false;
-    // 2: rejections and norms; a-priori errors against w_b
-    if (big_rej) phase_reject<Team, MIXED, 8>(T, S, gam, 0, b, r, S.C, nullptr);
-    else phase_reject<Team, MIXED, 1>(T, S, gam, 0, b, r, S.C, nullptr);
-    phase_dall(T, S, A, j0, b, r);
-    if (!T.sync()) return false;
-    // 3: decide
-    int q0;
-    if (b <= SMALL_B) {
-      q0 = decide_rows<MIXED>(S, A, j0, b, r, T.id() == 0);
-      if (q0 == b) {  // fast finish: every row dependent
-        acc_small(T, S, 0, b, r);
-        if (T.id() == 0) {
-          if (A.indep)
-            for (int j = threadIdx.x; j < b; j += NT) A.indep[j0 + j] = 0;
-          if (threadIdx.x == 0) {
-            *S.rows_seen = __ldcg(S.rows_seen) + b;
-            S.ctrl[CTRL_KB] = min(2 * kb0, S.kb_max);
-            S.ctrl[CTRL_PEND] = 1;
-          }
-        }
-        if (!last && !T.sync()) return false;
-        j0 += b;
-        continue;
+    // mixed mode, one CTA per stream, large blocks: projection, rejection norms and the
+    // FP32 screen on the tensor cores (q0 = first row the screen cannot clear)
+    int q0 = -2;
+    if constexpr (MIXED && std::is_same<Team, CtaTeam>::value) {
+      if (S.tcx && b > SMALL_B && r >= 1 && r <= TC_RMAX) {
+        double tcut = S.tau_lo;
+        if (S.test_mode == 0 && S.tol > 0.0) tcut = fmax(tcut, 0.5 * S.tol);
+        q0 = tc_project_block(reinterpret_cast<TcCtx*>(S.tcx), S, gam, A.y + j0, b, r, tcut);
+        if (q0 < 0) return false;
+        phase_dall(T, S, A, j0, b, r);
+        if (!T.sync()) return false;
       }
-    } else {
-      decide_rows_team<Team, MIXED>(T, S, A, j0, b, r);
+    }
+    if (q0 == -2) {
+      // 1: gamma of every row against the block-start basis
+      if (T.id() == 0 && threadIdx.x == 0) S.ctrl[CTRL_Q0] = b;
+      // larger items only while they still give every worker at least two
+      const bool big_rej = (long long)(b / 32) * S.nmc >= 2LL * T.size();
+      const int gr = min(8, (int)((POOL_DOUBLES * 2) / max(S.m, 1)));  // FP32 rows that fit
+      if (MIXED && gr >= 1 && (long long)(b / gr) >= 2LL * T.size())
+        phase_gamma_f32_staged(T, S, gam, 0, b, r, gr);
+      else
+        phase_gamma<Team, MIXED>(T, S, gam, 0, b, r, MIXED ? S.C : S.Ct);
       if (!T.sync()) return false;
-      if (threadIdx.x == 0) sh[3] = ld_acquire_i32(S.ctrl + CTRL_Q0);
-      __syncthreads();
-      q0 = sh[3];
+      // 2: rejections and norms; a-priori errors against w_b
+      if (big_rej) phase_reject<Team, MIXED, 8>(T, S, gam, 0, b, r, S.C, nullptr);
+      else phase_reject<Team, MIXED, 1>(T, S, gam, 0, b, r, S.C, nullptr);
+      phase_dall(T, S, A, j0, b, r);
+      if (!T.sync()) return false;
+      // 3: decide
+      if (b <= SMALL_B) {
+        q0 = decide_rows<MIXED>(S, A, j0, b, r, T.id() == 0);
+        if (q0 == b) {  // fast finish: every row dependent
+          acc_small<Team, MIXED>(T, S, 0, b, r);
+          if (T.id() == 0) {
+            if (A.indep)
+              for (int j = threadIdx.x; j < b; j += NT) A.indep[j0 + j] = 0;
+            if (threadIdx.x == 0) {
+              *S.rows_seen = __ldcg(S.rows_seen) + b;
+              S.ctrl[CTRL_KB] = min(2 * kb0, S.kb_max);
+              S.ctrl[CTRL_PEND] = 1;
+            }
+          }
+          if (!last && !T.sync()) return false;
+          j0 += b;
+          continue;
+        }
+      } else {
+        decide_rows_team<Team, MIXED>(T, S, A, j0, b, r);
+        if (!T.sync()) return false;
+        if (threadIdx.x == 0) sh[3] = ld_acquire_i32(S.ctrl + CTRL_Q0);
+        __syncthreads();
+        q0 = sh[3];
+      }
     }
     // 4: dependent run before the first special row
-    if (q0 > 0 && !dep_run(T, S, 0, q0, r)) return false;
+    if (q0 > 0 && !dep_run<Team, MIXED>(T, S, 0, q0, r)) return false;
     int applied = b, rnew = r;
     if (q0 < b) {
       // 5: sequential section, in FP64 (rows [q0, bend)); its rows never overlap the run
@@ -940,12 +1118,17 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       if (!T.sync()) return false;
       phase_reject<Team, false, 1>(T, S, gam, q0, bend, r, S.C, S.R);
       if (!T.sync()) return false;
-      int res[3];
-      if (!scan_team<Team, MIXED>(T, S, A, j0, q0, bend, r, res)) return false;
+      if (!scan_team<Team, MIXED>(T, S, A, j0, q0, bend, r)) return false;
       if (!T.sync()) return false;
-      applied = res[0];
-      rnew = res[1];
-      const int nind = res[2];
+      if (threadIdx.x == 0) {
+        sh[5] = ld_acquire_i32(S.ctrl + CTRL_APPLIED);
+        sh[6] = ld_acquire_i32(S.ctrl + CTRL_RNEW);
+        sh[7] = ld_acquire_i32(S.ctrl + CTRL_NIND);
+      }
+      __syncthreads();
+      applied = sh[5];
+      rnew = sh[6];
+      const int nind = sh[7];
       section_apply_pu<Team, MIXED>(T, S, q0, applied - q0, r, rnew);
       if (nind > 0) section_apply_basis<Team, MIXED>(T, S, A, j0, r, nind);
     }

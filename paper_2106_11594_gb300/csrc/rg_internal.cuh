@@ -35,6 +35,7 @@ enum : int {
   CTRL_RNEW = 8,       // block plan: rank after the block
   CTRL_NIND = 9,       // block plan: independent rows found in the block
   CTRL_PEND = 10,      // 1: u holds a correction not yet folded into w
+  CTRL_SUB_COUNT = 12, // barrier counter of the sequential section's column owners (words 12-13)
   CTRL_N = 16
 };
 
@@ -82,7 +83,34 @@ struct StreamDev {
   double* Lw;     // r_max x r_max: Cholesky workspace (solution, export)
   double* Sp;     // 2 x sp_stride: per-worker partial sums of the sequential section
   size_t sp_stride;  // >= 32 x (number of workers)
+  void* tcx;      // tensor-core context of the CTA (struct TcCtx in shared memory) or null
+  double* Kap;    // SLOW_MAX x SLOW_MAX: kappa of the section's later rows per append
+  double* Rs;     // shared memory for the section's rejections (one-CTA team) or null
+  long long rs_cap;  // doubles available at Rs
 };
+
+// FP64 -> FP32 by integer operations, rounding toward zero (FP64<->FP32 conversion
+// instructions issue on the FP64 pipe, 1/64 of the FP32 rate on this part). Magnitudes
+// below the FP32 normal range give a signed zero, above it a signed infinity; NaN stays
+// NaN.
+__device__ __forceinline__ float d2f_rz(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned ex = hi & 0x7FF00000u, sign = hi & 0x80000000u;
+  unsigned f = sign | ((((hi & 0x7FFFFFFFu) - (896u << 20)) << 3) | (lo >> 29));
+  if (ex < (897u << 20)) f = sign;
+  if (ex >= (1151u << 20)) f = sign | 0x7F800000u | ((ex == 0x7FF00000u && ((hi & 0xFFFFFu) | lo)) ? 0x400000u : 0u);
+  return __uint_as_float(f);
+}
+
+// FP32 -> FP64 (exact) by integer operations for normal numbers, zero, infinity and NaN;
+// FP32 subnormals take the conversion instruction.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xFFu, sign = u & 0x80000000u, man = u & 0x7FFFFFu;
+  if (ex == 0u) return man ? (double)f : __hiloint2double((int)sign, 0);
+  const unsigned hex = (ex == 0xFFu) ? 0x7FF00000u : ((ex + 896u) << 20);
+  return __hiloint2double((int)(sign | hex | (man >> 3)), (int)(man << 29));
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

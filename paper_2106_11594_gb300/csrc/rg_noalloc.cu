@@ -72,6 +72,9 @@ size_t noalloc_layout(StreamDev& S, char* base) {
   S.jind = (int*)take(SLOW_MAX * 4);
   S.Dall = (double*)take(kb * 8);
   S.Lw = (double*)take(rm * rm * 8);
+  S.Kap = (double*)take((size_t)SLOW_MAX * SLOW_MAX * 8);
+  S.Rs = nullptr;
+  S.rs_cap = 0;
   S.sp_stride = (size_t)32 * std::min<size_t>((ld + NT - 1) / NT, 1024);  // <= 1024 workers
   S.Sp = (double*)take(2 * S.sp_stride * 8);
   S.Pp = nullptr;  // no chunked partial sums here: long runs accumulate directly

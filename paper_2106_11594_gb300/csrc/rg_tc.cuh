@@ -1,0 +1,381 @@
+// rg_tc.cuh -- the block projection of mixed mode on the fifth-generation tensor cores
+// (tcgen05.mma, kind::tf32, FP32 accumulators in tensor memory).
+//
+// For a chunk of up to 128 rows of a block (Section 3's block of observations, all
+// projected against the block-start basis Q, which dependent rows leave unchanged by
+// Theorem 6) one CTA computes
+//   G = Gamma_c Q^T          (128 x r: the coordinates gamma_j of the rows, Section 2.2)
+//   R = Gamma_c - G Q        (128 x m: the rejections, Eq. label_eq_schur_complement)
+// and from R the squared norms s_j = ||Gamma_r,j||^2 and t_j = ||Gamma_j||^2 of the FP32
+// screen of mixed mode. Both products are dense contractions (K = m, then K = r) and run as
+// 3xTF32: every FP32 operand x is split into hi = x rounded to TF32 and lo = x - hi, and
+// A B = Ahi Bhi + Ahi Blo + Alo Bhi, which keeps the product error near FP32 rounding
+// (one TF32 product alone would leave a rejection noise of ~1e-3 |Gamma|, far above the
+// screen's floor tau_lo).
+//
+// Operands are staged by all threads into shared memory in the no-swizzle K-major
+// core-matrix layout (core matrix = 8 rows x 16 bytes, 128 contiguous bytes; the next
+// core matrix along K at +128 B, the next 8-row group at +1024 B for a 32-wide K slice);
+// one thread issues the MMAs and commits them to an mbarrier; the accumulators are read
+// back with tcgen05.ld (32x32b shape: thread = row). Waits on the mbarrier are bounded.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rg_internal.cuh"
+
+namespace rg {
+
+constexpr int TC_M = 128;      // rows per chunk (MMA M)
+constexpr int TC_K = 32;       // K slice: 32 TF32 elements = 128 bytes per row
+constexpr int TC_N2 = 64;      // columns of m per second-product slice (MMA N)
+constexpr int TC_RMAX = 128;   // ranks handled (first-product N = r rounded up to 16)
+constexpr int TC_TILE = TC_M * TC_K;            // floats per operand tile (16 KiB)
+constexpr int TC_SMEM = 4 * TC_TILE * 4 + 1024;  // Ahi, Alo, Bhi, Blo + alignment slack
+constexpr int TC_TMEM_COLS = 256;               // D1: columns [0, 128); D2: [128, 192)
+
+// Per-CTA tensor-core context (shared memory, written once by the kernel prologue except
+// `phase`, which thread 0 stores back at the end of every projection).
+struct TcCtx {
+  float* Ahi;
+  float* Alo;
+  float* Bhi;
+  float* Blo;
+  unsigned long long* bar;  // mbarrier: one arrival per commit
+  uint32_t tmem;            // tensor-memory base (lane 0, column 0)
+  uint32_t phase;           // parity of the next completion of `bar`
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Offset (floats) of element (row, k) in a tile with a 32-wide K slice.
+__host__ __device__ __forceinline__ int tc_off(int row, int k) {
+  return (row >> 3) * 256 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
+}
+
+// Shared-memory matrix descriptor: start address, leading byte offset 128 (K direction),
+// stride byte offset 1024 (8-row groups), fixed version bits, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(128u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor: D FP32, A and B TF32, both K-major, N >> 3 and M >> 4.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Every thread waits for the completion of parity `ph` of the mbarrier (bounded); the CTA
+// agrees on the outcome. On success the parity advances; false if the wait gave up.
+__device__ __forceinline__ bool tc_wait(unsigned long long* bar, uint32_t& ph) {
+  bool done = mbar_try_wait(bar, ph);
+  if (!done) {
+    const unsigned long long t0 = global_ns();
+    while (!(done = mbar_try_wait(bar, ph)))
+      if (global_ns() - t0 > WAIT_LIMIT_NS) break;
+  }
+  if (!__syncthreads_and(done ? 1 : 0)) return false;
+  ph ^= 1u;
+  tc_fence_after();
+  return true;
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// hi = x rounded to TF32 (10 explicit mantissa bits), lo = x - hi (exact in FP32).
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+  lo = x - hi;
+}
+
+// One 32-wide K slice of D (+)= A B^T as 3xTF32 (four K steps of 8), issued by one thread.
+__device__ __forceinline__ void tc_slice_mma(const TcCtx& X, uint32_t d, int N, bool first) {
+  const uint32_t id = tc_idesc(TC_M, N);
+  const uint32_t ah = smem_u32(X.Ahi), al = smem_u32(X.Alo), bh = smem_u32(X.Bhi), bl = smem_u32(X.Blo);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const uint32_t o = (uint32_t)s * 256u;  // 8 TF32 = two core matrices along K
+    tc_mma(d, tc_desc(ah + o), tc_desc(bh + o), id, (first && s == 0) ? 0u : 1u);
+    tc_mma(d, tc_desc(ah + o), tc_desc(bl + o), id, 1u);
+    tc_mma(d, tc_desc(al + o), tc_desc(bh + o), id, 1u);
+  }
+}
+
+// A = rows [0, 128) x columns [k0, k0 + 32) of an FP64 row-major matrix (valid rows <
+// nrows, valid columns < m; the rest zero), in two steps so that the loads of the next
+// slice can be in flight while the tensor cores work on the current one: tc_load_a puts
+// this thread's 16 elements in registers (FP32), tc_store_a splits and stores them. Warp w
+// takes the 4 columns [4w, 4w + 4) of all 16 row groups; a warp access covers 8 rows x 4
+// columns, so its 32 lanes hit 32 distinct banks.
+// The 16 loads are all issued before any value is used (raw FP64 kept in registers), so
+// they are in flight together; the conversion happens in tc_store_a.
+__device__ __forceinline__ void tc_load_a(double (&v)[16], const double* __restrict__ src, int m, int nrows,
+                                          int k0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rl = lane >> 2, c = k0 + warp * 4 + (lane & 3);
+  const bool cok = c < m;
+  const double* p = src + (size_t)rl * m + c;
+#pragma unroll
+  for (int rg = 0; rg < 16; ++rg)
+    v[rg] = (cok && rg * 8 + rl < nrows) ? __ldg(p + (size_t)rg * 8 * m) : 0.0;
+}
+__device__ __forceinline__ void tc_store_a(const TcCtx& X, const double (&v)[16]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int o0 = warp * 32 + (lane >> 2) * 4 + (lane & 3);
+#pragma unroll
+  for (int rg = 0; rg < 16; ++rg) {
+    float h, l;
+    tf32_split(d2f_rz(v[rg]), h, l);
+    X.Ahi[o0 + rg * 256] = h;
+    X.Alo[o0 + rg * 256] = l;
+  }
+}
+
+// Stages B = rows [0, nrow) (multiple of 8) x columns [k0, k0 + 32) of the FP32 basis Qf
+// (rows >= r and columns >= m zero).
+__device__ __forceinline__ void tc_stage_q(const TcCtx& X, const float* __restrict__ Qf, int ld, int m,
+                                           int r, int nrow, int k0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rl = lane >> 2, kl = lane & 3;
+  // warp w takes column group kg = w of the row groups rg < nrow / 8 (at most 16); all
+  // loads are issued before the stores
+  const int c = k0 + warp * 4 + kl;
+  const int ngr = nrow >> 3;
+  float x[16];
+#pragma unroll
+  for (int rg = 0; rg < 16; ++rg) {
+    const int row = rg * 8 + rl;
+    x[rg] = (rg < ngr && row < r && c < m) ? __ldcg(Qf + (size_t)row * ld + c) : 0.f;
+  }
+  const int o0 = warp * 32 + rl * 4 + kl;
+#pragma unroll
+  for (int rg = 0; rg < 16; ++rg) {
+    if (rg < ngr) {
+      float h, l;
+      tf32_split(x[rg], h, l);
+      X.Bhi[o0 + rg * 256] = h;
+      X.Blo[o0 + rg * 256] = l;
+    }
+  }
+}
+
+// Stages B = Q^T slice for the second product: row n < 64 is column c0 + n of Q, K index
+// k is basis row k1 + k (zero beyond r or m). Threads [t_lo, t_lo + 128) take part.
+__device__ __forceinline__ void tc_stage_qt(const TcCtx& X, const float* __restrict__ Qf, int ld, int m,
+                                            int r, int c0, int k1, int t_lo) {
+  const int t = threadIdx.x - t_lo;
+  const int lane = t & 31, warp = t >> 5;  // 4 warps
+  const int rl = lane >> 2, kl = lane & 3;
+  float x[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int it = warp + 4 * q;
+    const int rg = it >> 3, kg = it & 7;
+    const int n = rg * 8 + rl, i = k1 + kg * 4 + kl, c = c0 + n;
+    x[q] = (i < r && c < m) ? __ldcg(Qf + (size_t)i * ld + c) : 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int it = warp + 4 * q;
+    const int rg = it >> 3, kg = it & 7;
+    float h, l;
+    tf32_split(x[q], h, l);
+    const int o = rg * 256 + kg * 32 + rl * 4 + kl;
+    X.Bhi[o] = h;
+    X.Blo[o] = l;
+  }
+}
+
+// A wait gave up: wait once more (bounded) for the MMAs in flight, so that the caller can
+// release its shared and tensor memory, record ST_TIMEOUT and report failure.
+__device__ __forceinline__ int tc_timeout(const StreamDev& S, TcCtx* Xp, uint32_t ph) {
+  if (tc_wait(Xp->bar, ph) && threadIdx.x == 0) Xp->phase = ph;
+  if (threadIdx.x == 0) atomicOr(S.ctrl + CTRL_STATUS, ST_TIMEOUT);
+  __syncthreads();
+  return -1;
+}
+
+// Block rows [0, b) against the basis (rank 1 <= r <= TC_RMAX), mixed mode, one CTA:
+// writes S.G (FP64 copies of the FP32 gammas), S.s and S.t, and returns the first row
+// that the FP32 screen cannot declare dependent (b if none), or -1 if a bounded wait gave
+// up (ST_TIMEOUT is then set in the status word; MMAs may still be in flight). The rows
+// are Gamma[j * m ...] of `gam`, their targets y[j].
+static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const double* __restrict__ gam,
+                                const double* __restrict__ y, int b, int r, double tc) {
+  __shared__ int q0_s;
+  const TcCtx X = *Xp;
+  uint32_t ph = X.phase;
+  __shared__ float red_s[TC_M], red_t[TC_M];
+  const int m = S.m, ld = S.ld, rm = S.r_max;
+  const int n1 = (r + 15) & ~15;             // first-product N (16..128)
+  const int nks = (m + TC_K - 1) / TC_K;     // K slices of the first product
+  const int nns = (m + TC_N2 - 1) / TC_N2;   // N slices of the second product
+  const int nk2 = (r + TC_K - 1) / TC_K;     // K slices of the second product
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3, half = warp >> 2;
+  const uint32_t d1 = X.tmem, d2 = X.tmem + 128u;
+  const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+  if (threadIdx.x == 0) q0_s = b;
+  for (int row0 = 0; row0 < b; row0 += TC_M) {
+    const int nrows = min(TC_M, b - row0);
+    const double* src = gam + (size_t)row0 * m;
+    // ---- first product: G = Gamma_c Q^T over K slices of m; the next slice's rows are
+    // loaded while the tensor cores work on the current one
+    double av[16];
+    tc_load_a(av, src, m, nrows, 0);
+    for (int ks = 0; ks < nks; ++ks) {
+      tc_store_a(X, av);
+      tc_stage_q(X, S.Qf, ld, m, r, n1, ks * TC_K);
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        tc_slice_mma(X, d1, n1, ks == 0);
+        tc_commit(X.bar);
+      }
+      if (ks + 1 < nks) tc_load_a(av, src, m, nrows, (ks + 1) * TC_K);
+      if (!tc_wait(X.bar, ph)) return tc_timeout(S, Xp, ph);
+    }
+    // ---- G to global (FP64), threads of warps 0-3 own rows
+    const int row = quarter * 32 + lane;
+    if (half == 0) {
+      for (int i0 = 0; i0 < n1; i0 += 32) {
+        float g[32];
+        tmem_ld32(d1 + lane_base + (uint32_t)i0, g);
+        if (row < nrows) {
+          double* gout = S.G + (size_t)(row0 + row) * rm;
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (i0 + q < r) gout[i0 + q] = f2d_exact(g[q]);
+        }
+      }
+    }
+    // ---- second product per 64-column slice: GQ, then R = Gamma - GQ and the norms
+    float s_acc = 0.f, t_acc = 0.f;
+    for (int ns = 0; ns < nns; ++ns) {
+      const int c0 = ns * TC_N2;
+      for (int k2 = 0; k2 < nk2; ++k2) {
+        if (half == 0) {
+          if (nk2 > 1 || ns == 0) {  // A = G slice (unchanged across column slices if r <= 32)
+            float g[32];
+            tmem_ld32(d1 + lane_base + (uint32_t)(k2 * TC_K), g);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              float h, l;
+              tf32_split(k2 * TC_K + q < r ? g[q] : 0.f, h, l);
+              const int o = tc_off(row, q);
+              X.Ahi[o] = h;
+              X.Alo[o] = l;
+            }
+          }
+        } else {
+          tc_stage_qt(X, S.Qf, ld, m, r, c0, k2 * TC_K, 128);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          tc_fence_after();
+          tc_slice_mma(X, d2, TC_N2, k2 == 0);
+          tc_commit(X.bar);
+        }
+        if (!tc_wait(X.bar, ph)) return tc_timeout(S, Xp, ph);
+      }
+      // epilogue: warp w reads lanes of its quarter, columns [32 half, 32 half + 32)
+      float gq[32];
+      tmem_ld32(d2 + lane_base + (uint32_t)(half * 32), gq);
+      if (row < nrows) {
+        const double* xr = src + (size_t)row * m;
+        const int cb = c0 + half * 32;
+#pragma unroll
+        for (int h2 = 0; h2 < 32; h2 += 16) {
+          double xv[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) xv[q] = (cb + h2 + q < m) ? __ldg(xr + cb + h2 + q) : 0.0;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const float xf = d2f_rz(xv[q]);
+            const float rv = (cb + h2 + q < m) ? xf - gq[h2 + q] : 0.f;
+            s_acc = fmaf(rv, rv, s_acc);
+            t_acc = fmaf(xf, xf, t_acc);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();  // D2 and the staging buffers are free again
+      tc_fence_after();
+    }
+    // ---- combine the two column halves of each row, store s, t, screen
+    if (half == 1) {
+      red_s[row] = s_acc;
+      red_t[row] = t_acc;
+    }
+    __syncthreads();
+    if (half == 0 && row < nrows) {
+      const double s = (double)(s_acc + red_s[row]), t = (double)(t_acc + red_t[row]);
+      const int j = row0 + row;
+      S.s[j] = s;
+      S.t[j] = t;
+      const double yv = __ldg(y + j);
+      if (!isfinite(yv) || !(t > 1e-30 && t < 1e30 && s <= tc * tc * t)) atomicMin(&q0_s, j);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) Xp->phase = ph;
+  const int q0 = q0_s;
+  __syncthreads();
+  return q0;
+}
+
+}  // namespace rg

@@ -67,6 +67,34 @@ def test_ragged_and_degenerate_instances():
         assert_batch(g, batch, ores, tol if mode == rg.RG_FP64 else 1e-3)
 
 
+# Mixed-mode shapes around the tensor-core block projection (128-row chunks, 32-wide K
+# slices of m, 64-wide column slices, first-product N = r rounded up to 16, ranks up to
+# 128; r > 128 takes the FP32 CUDA-core path): ragged m, ragged r, a zero row, rank growth
+# after many dependent rows, and blocks whose last chunk is partial.
+TC_SHAPES = [(700, 77, 5), (600, 200, 40), (500, 130, 100), (400, 512, 128), (450, 300, 140),
+             (1000, 33, 16), (333, 64, 17), (900, 96, 32)]
+
+
+def test_mixed_tensor_core_shapes():
+    rng = inputs.rng_for(401, 0)
+    streams = []
+    for k, (n, m, r) in enumerate(TC_SHAPES):
+        G1 = rng.standard_normal((n, r))
+        G2 = rng.standard_normal((r, m))
+        if k == 6:  # rank growth late: rows 250+ gain two new directions
+            G1[:250, -2:] = 0.0
+        A = np.ascontiguousarray(G1 @ G2)
+        if k == 1:
+            A[300] = 0.0
+        Y = A @ rng.standard_normal(m) + 1e-4 * rng.standard_normal(n)
+        streams.append(inputs.Stream(A=A, Y=Y, rank=min(n, m, r)))
+    batch = inputs.Batch(streams=streams)
+    ores = oracle_batch(batch)
+    for calls in (1, 3):
+        g = run_batch(batch, mode=rg.RG_MIXED, calls=calls)
+        assert_batch(g, batch, ores, 1e-4)
+
+
 def test_single_instance_batch_matches_stream_api():
     s = inputs.large_stream(1500, 200, 20)
     batch = inputs.Batch(streams=[s])
