@@ -210,7 +210,7 @@ rg_status rg_batch_free(rg_batch* bt);
  *   cuda_stream  cudaStream_t for all work (NULL: legacy default stream).
  * State and scratch live in one fixed file-scope device array of 8 MiB that every GPU
  * loading the library holds until the process exits; a problem whose state and scratch do
- * not fit (with r_max = m: m above 495 in FP64, above 528 in mixed mode; a smaller r_max
+ * not fit (with r_max = m: m above 494 in FP64, above 528 in mixed mode; a smaller r_max
  * raises the limit) is rejected with RG_EINVAL and a message.
  * Every call shares that array and clears what must start at zero itself; calls that
  * overlap on the GPU (different streams or host threads) race on it and must be

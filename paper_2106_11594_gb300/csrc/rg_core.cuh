@@ -79,6 +79,16 @@ __device__ __forceinline__ double rsqrt_nr(double d) {
   return y;
 }
 
+// 1/d for d > 0: single-precision seed refined by two Newton-Raphson steps
+// y <- y (2 - d y) (quadratic convergence, as for rsqrt_nr); 1/d outside that range.
+__device__ __forceinline__ double rcp_nr(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
+  double y = (double)(1.0f / (float)d);
+  y = y * fma(-d, y, 2.0);
+  y = y * fma(-d, y, 2.0);
+  return y;
+}
+
 // CTA-wide sum; every thread gets the result.
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double red[NWARP];
@@ -733,12 +743,19 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
                           int bend, int r) {
   const int m = S.m, ld = S.ld, rm = S.r_max;
   const int nrow = bend - q0;
-  const int nact = (int)min((long long)T.size(), ((long long)m + NT - 1) / NT);
+  // grid teams: one warp per CTA owns 32 columns (registers), so that the FP64 work of a
+  // row (partials, their reduction, the fix-ups) spreads over ceil(m / 32) SMs; otherwise
+  // (one-CTA teams, or m beyond 32 columns per CTA) every thread owns columns
+  constexpr bool kGrid = std::is_same<Team, GridTeam>::value;
+  const long long nwarp_cols = ((long long)m + 31) / 32;
+  const bool reg = kGrid && nwarp_cols <= T.size() && nwarp_cols <= 20 * NWARP;
+  const int nact = reg ? (int)nwarp_cols : (int)min((long long)T.size(), ((long long)m + NT - 1) / NT);
   __shared__ double tot[32];
   __shared__ double wred[NWARP][32];
-  __shared__ double ts[32], ys[32], ss[32];
+  __shared__ double ts[32], ys[32], sq_s[32];  // t_j, y_j, sqrt(s_j) of the section rows
   __shared__ int flag_s[32];
   __shared__ int dec_s;
+  __shared__ double is_s, rsq_s;  // 1 / s_j and 1 / sqrt(s_j) of an independent row
   const int tid = threadIdx.x;
   int rc = r, nind = 0, applied = bend;
   if (T.id() < nact) {
@@ -755,9 +772,7 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
     }
     __syncthreads();
     unsigned long long bar_target = bar_target_s;
-    // grid teams with one column per thread keep the rejections in registers
     const long long cstride = (long long)nact * NT;
-    constexpr bool kGrid = std::is_same<Team, GridTeam>::value;
     // decision of row jj (thread 0), records (worker 0), kappa of the later rows
     auto decide = [&](int jj) -> int {
       const int j = q0 + jj;
@@ -766,51 +781,83 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
         int d = 0;
         if (!isfinite(t) || !isfinite(yv) || !isfinite(s)) d = -1;
         else if (is_independent(s, t, rc, m, S.tol, S.test_mode)) d = (rc >= rm) ? -2 : 1;
+        // the reciprocals are formed once, here, by Newton-Raphson (FP64 division and
+        // square root are long dependent chains on this part)
+        const double is = (d == 1) ? rcp_nr(s) : 0.0, rsq = (d == 1) ? rsqrt_nr(s) : 0.0;
         if (T.id() == 0) {
           if (d < 0) {
             atomicOr(S.ctrl + CTRL_STATUS, d == -1 ? ST_NONFINITE : ST_CAPACITY);
           } else {
             flag_s[jj] = d + 1;
             S.rowflag[j] = (uint8_t)(d + 1);
-            ss[jj] = s;
+            sq_s[jj] = s * rsq;
             if (d == 1) {
               S.jind[nind] = j;
-              S.alpha[nind] = 1.0 / sqrt(s);
+              S.alpha[nind] = rsq;
               S.basis_rows[rc] = base_row + j;
               S.wb[rc] = ORTHO ? 0.0 : yv;  // w_b <- [w_b; y] (general) or [w_b; 0] (orthonormal)
             }
           }
         }
+        is_s = is;
+        rsq_s = rsq;
         dec_s = d;
       }
       __syncthreads();
       const int d = dec_s;
       if (d == 1 && T.id() == 0 && tid >= 1 && tid < 32 && jj + tid < nrow)
-        S.Kap[nind * SLOW_MAX + jj + tid] = tot[tid] / tot[0];
+        S.Kap[nind * SLOW_MAX + jj + tid] = tot[tid] * is_s;
       return d;
     };
-    bool done = false;
     if constexpr (kGrid) {
-      if ((long long)m <= cstride) {
-      done = true;
-      const long long c = (long long)T.id() * NT + tid;
-      const bool cv = c < m;
+      if (reg) {
+      const int lane = tid & 31, warp = tid >> 5;
+      const long long c = (long long)T.id() * 32 + lane;
+      const bool cv = warp == 0 && c < m;
       double R[32];
 #pragma unroll
       for (int k = 0; k < 32; ++k) R[k] = (cv && k < nrow) ? __ldcg(S.R + (size_t)k * ld + c) : 0.0;
       for (int jj = 0; jj < nrow; ++jj) {
-        double v[32];
+        if (warp == 0) {
+          double v[32];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) v[k] = R[0] * R[k];
-        if (!scan_exchange(T, S, v, nact, jj & 1, bar_target, tot, wred)) return false;
+          for (int k = 0; k < 32; ++k) v[k] = R[0] * R[k];
+          warp_transpose_sum32(v);  // lane k: this CTA's part of value k
+          if (nact > 1) S.Sp[(size_t)(jj & 1) * S.sp_stride + (size_t)T.id() * 32 + lane] = v[0];
+          else tot[lane] = v[0];
+        }
+        if (nact > 1) {
+          if (!sub_barrier(S.ctrl, nact, bar_target)) return false;
+          // value k = lane, summed over the owners w = warp, warp + NWARP, ... then over warps
+          // (all loads issued before the adds: up to 20 owners per warp)
+          const double* Sp = S.Sp + (size_t)(jj & 1) * S.sp_stride;
+          double pv[20];
+#pragma unroll
+          for (int q = 0; q < 20; ++q) {
+            const int w2 = warp + q * NWARP;
+            pv[q] = (w2 < nact) ? __ldcg(Sp + (size_t)w2 * 32 + lane) : 0.0;
+          }
+          double a = 0.0;
+#pragma unroll
+          for (int q = 0; q < 20; ++q) a += pv[q];
+          wred[warp][lane] = a;
+          __syncthreads();
+          if (tid < 32) {
+            double t2 = 0.0;
+#pragma unroll
+            for (int w2 = 0; w2 < NWARP; ++w2) t2 += wred[w2][tid];
+            tot[tid] = t2;
+          }
+        }
+        __syncthreads();
         const int d = decide(jj);
         if (d < 0) {
           applied = q0 + jj;
           break;
         }
         if (d == 1) {
-          const double s = tot[0], is = 1.0 / s;
-          const double scale = ORTHO ? 1.0 / sqrt(s) : is;
+          const double is = is_s;
+          const double scale = ORTHO ? rsq_s : is;
           if (cv) S.Kv[(size_t)nind * ld + c] = R[0] * scale;
 #pragma unroll
           for (int k = 1; k < 32; ++k) R[k] = fma(-tot[k] * is, R[0], R[k]);
@@ -823,7 +870,7 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
       }
       }
     }
-    if (!done) {
+    if (!reg) {
       // rejections in shared memory (row stride m) when they fit, else in S.R (global,
       // read through L2 since other CTAs wrote it); `rsm` selects plain shared-memory loads
       double* Rb = S.R;
@@ -858,8 +905,8 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
           break;
         }
         if (d == 1) {
-          const double s = tot[0], is = 1.0 / s;
-          const double scale = ORTHO ? 1.0 / sqrt(s) : is;
+          const double is = is_s;
+          const double scale = ORTHO ? rsq_s : is;
           for (long long c = col0; c < m; c += cstride) {
             const double rj = rload(Rb + (size_t)jj * ldr + c);
             S.Kv[(size_t)nind * ld + c] = rj * scale;
@@ -877,8 +924,12 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
     }
   }
   if (T.id() == 0) {
-    // replay the appends on the coordinates: thread = coordinate i (of the final rank rc)
+    // replay the appends on the coordinates: thread = coordinate i (of the final rank rc);
+    // the kappas are staged in the shared pool first
     const int napp = applied - q0;
+    __syncthreads();
+    double* kap_s = smem_pool();
+    for (int e = tid; e < nind * SLOW_MAX; e += NT) kap_s[e] = __ldcg(S.Kap + e);
     __syncthreads();
     for (int i0 = 0; i0 < rc; i0 += NT) {
       const int i = i0 + tid;
@@ -892,11 +943,11 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
           if (i < rcv) S.G[(size_t)(q0 + tt) * rm + i] = g[tt];
           if (flag_s[tt] == 2) {
             if (i < rcv) S.Gind[(size_t)q * rm + i] = g[tt];
-            const double sq = sqrt(ss[tt]);
+            const double sq = sq_s[tt];
 #pragma unroll
             for (int t2 = tt + 1; t2 < 32; ++t2) {
               if (t2 < napp) {
-                const double kap = __ldcg(S.Kap + q * SLOW_MAX + t2);
+                const double kap = kap_s[q * SLOW_MAX + t2];
                 if (i < rcv) {
                   if (!ORTHO) g[t2] = fma(-kap, g[tt], g[t2]);
                 } else if (i == rcv) {

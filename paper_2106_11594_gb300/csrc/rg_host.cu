@@ -50,7 +50,7 @@ rg_status status_from_bits(int bits) {
 }
 
 __global__ void reset_kernel(int* ctrl, long long* rows_seen, int kb0) {
-  if (threadIdx.x < CTRL_N) ctrl[threadIdx.x] = 0;
+  for (int i = threadIdx.x; i < CTRL_N; i += blockDim.x) ctrl[i] = 0;
   __syncthreads();
   if (threadIdx.x == 0) {
     ctrl[CTRL_KB] = kb0;
@@ -130,7 +130,7 @@ size_t carve(StreamDev& S, char* base) {
   S.Kap = cv.take<double>((size_t)SLOW_MAX * SLOW_MAX);
   S.Rs = nullptr;
   S.rs_cap = 0;
-  S.sp_stride = (size_t)32 * std::min<size_t>((ld + NT - 1) / NT, 1024);  // <= 1024 workers
+  S.sp_stride = (size_t)32 * std::min<size_t>((ld + 31) / 32, 1024);  // <= 1024 workers
   S.Sp = cv.take<double>(2 * S.sp_stride);
   return align_up(cv.off, 256);
 }

@@ -35,8 +35,9 @@ enum : int {
   CTRL_RNEW = 8,       // block plan: rank after the block
   CTRL_NIND = 9,       // block plan: independent rows found in the block
   CTRL_PEND = 10,      // 1: u holds a correction not yet folded into w
-  CTRL_SUB_COUNT = 12, // barrier counter of the sequential section's column owners (words 12-13)
-  CTRL_N = 16
+  CTRL_SUB_COUNT = 32, // barrier counter of the sequential section's column owners (words
+                       // 32-33, a cache line apart from the grid barrier's counter)
+  CTRL_N = 64
 };
 
 // Everything a kernel needs to know about one stream. Plain pointers into device
@@ -179,11 +180,13 @@ __device__ __forceinline__ bool grid_barrier(int* ctrl) {
     if (ld_acquire_u64(cnt) < target) {
       const unsigned long long t0 = global_ns();
       while (ld_acquire_u64(cnt) < target) {
-        if (global_ns() - t0 > WAIT_LIMIT_NS) {
+        const unsigned long long dt = global_ns() - t0;
+        if (dt > WAIT_LIMIT_NS) {
           atomicOr(ctrl + CTRL_STATUS, ST_TIMEOUT);
           ok = 0;
           break;
         }
+        if (dt > 4000) __nanosleep(256);  // long waits (a few CTAs busy) poll gently
       }
     }
   }

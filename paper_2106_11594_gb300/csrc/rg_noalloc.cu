@@ -75,7 +75,7 @@ size_t noalloc_layout(StreamDev& S, char* base) {
   S.Kap = (double*)take((size_t)SLOW_MAX * SLOW_MAX * 8);
   S.Rs = nullptr;
   S.rs_cap = 0;
-  S.sp_stride = (size_t)32 * std::min<size_t>((ld + NT - 1) / NT, 1024);  // <= 1024 workers
+  S.sp_stride = (size_t)32 * std::min<size_t>((ld + 31) / 32, 1024);  // <= 1024 workers
   S.Sp = (double*)take(2 * S.sp_stride * 8);
   S.Pp = nullptr;  // no chunked partial sums here: long runs accumulate directly
   S.pp_cap = 0;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(NT, 1) noalloc_kernel(StreamDev S, CallArgs A)
 // Clears what must start at zero before each call: the control words (rank, status,
 // grid-barrier counter and generation, block plan) and the row counter.
 __global__ void noalloc_reset_kernel(int* ctrl, long long* rows_seen, int kb0) {
-  if (threadIdx.x < CTRL_N) ctrl[threadIdx.x] = 0;
+  for (int i = threadIdx.x; i < CTRL_N; i += blockDim.x) ctrl[i] = 0;
   __syncthreads();
   if (threadIdx.x == 0) {
     ctrl[CTRL_KB] = kb0;
