@@ -110,6 +110,25 @@ rg_status rg_add_rows_host(rg_state* st, const double* Gamma, const double* y, i
  */
 rg_status rg_solution(rg_state* st, double* X, int64_t* rank_out);
 
+/*
+ * rg_adjoint -- gradient of a loss L(X) through X = A^+ y, from the state's final
+ * factorization. The paper has no counterpart: it is the classical derivative of the
+ * pseudoinverse on the manifold of fixed-rank matrices (from the Penrose equations of
+ * Section 1), evaluated with A^+ = Ct^T P^-1 B^T (Section 2.1):
+ *   dL/dy = h = A^+T g,   dL/dA = -h X^T + rho (A^+ h)^T + (A^+T X) g_perp^T,
+ *   rho = y - A X,        g_perp = (I - A^+ A) g.
+ *   A     device FP64, n x m row-major: exactly the rows fed since init/reset, in order
+ *         (the library does not keep them).
+ *   y     device FP64, n: their targets.
+ *   g     device FP64, m: dL/dX.
+ *   gA    device FP64, n x m (output);  gy  device FP64, n (output).
+ *   X     device FP64, m, may be NULL: receives X.
+ * FP64 throughout, in both modes. Uses a stream-ordered workspace (cudaMallocAsync) of
+ * about 8 (4m + 7 r_max + 3n + 4 m ceil(n/256)) bytes. Asynchronous.
+ */
+rg_status rg_adjoint(rg_state* st, const double* A, const double* y, int64_t n, const double* g,
+                     double* gA, double* gy, double* X);
+
 /* rg_solution_host -- rg_solution into HOST memory X (m doubles). Synchronising. */
 rg_status rg_solution_host(rg_state* st, double* X, int64_t* rank_out);
 
@@ -184,6 +203,19 @@ rg_status rg_batch_add_rows(rg_batch* bt, const double* Gamma_packed,
  */
 rg_status rg_batch_solution(rg_batch* bt, double* X_packed, const int64_t* x_offsets,
                             int64_t* ranks_out);
+
+/*
+ * rg_batch_adjoint -- rg_adjoint for every instance, one launch. The rows, offsets and
+ * targets are laid out as in rg_batch_add_rows and must be all rows fed since
+ * init/reset; total_rows (host) is row_offsets[B]. g_packed holds dL/dX of instance b at
+ * x_offsets[b] (NULL: packed by m_b); gA_packed is laid out like Gamma_packed, gy_packed
+ * like y_packed. Inconsistent offsets set RG_EINVAL on the instance (reported by the next
+ * rg_batch_sync). FP64 throughout. Asynchronous.
+ */
+rg_status rg_batch_adjoint(rg_batch* bt, const double* Gamma_packed, const int64_t* row_offsets,
+                           const int64_t* elem_offsets, const double* y_packed, int64_t total_rows,
+                           const double* g_packed, const int64_t* x_offsets, double* gA_packed,
+                           double* gy_packed);
 
 /* rg_batch_sync -- wait and return any pending device error of the batch. */
 rg_status rg_batch_sync(rg_batch* bt);

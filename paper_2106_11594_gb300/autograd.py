@@ -1,0 +1,68 @@
+"""torch.autograd.Function around the rank-Greville solve: X = A^+ y forward on the GPU
+(rg_init / rg_add_rows / rg_solution), and the adjoint kernel (rg_adjoint) backward.
+
+The gradient is the derivative of the minimum-norm least-squares solution on the manifold
+of matrices of fixed rank: for a rank-deficient A it is exact along perturbations that
+keep the rank (for example perturbations of the factors of A = G1 G2); a generic
+perturbation of a rank-deficient A changes the rank, where A^+ is not differentiable.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import rg
+
+
+class _LstsqRG(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, A, y, tol, mode):
+        A = A.contiguous()
+        y = y.contiguous()
+        st = rg.RankGreville(A.shape[1], tol, mode)
+        if A.shape[0] > 0:
+            st.add_rows(A, y)
+        X = torch.empty(A.shape[1], dtype=torch.float64, device=A.device)
+        st.solution(X, with_rank=False)
+        ctx.st = st
+        ctx.save_for_backward(A, y)
+        return X
+
+    @staticmethod
+    def backward(ctx, gX):
+        A, y = ctx.saved_tensors
+        gA = torch.empty_like(A)
+        gy = torch.empty_like(y)
+        ctx.st.adjoint(A, y, gX.contiguous(), gA, gy)
+        return gA, gy, None, None
+
+
+def lstsq_rg(A, y, tol: float = 1e-10, mode: int = rg.RG_FP64):
+    """X = A^+ y for A (n, m) and y (n,) float64 CUDA tensors, differentiable in A and y."""
+    return _LstsqRG.apply(A, y, tol, mode)
+
+
+class _LstsqRGBatch(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, A_packed, y_packed, row_offsets, elem_offsets, m_list, tol, mode):
+        bt = rg.RankGrevilleBatch(m_list, tol, mode)
+        bt.add_rows(A_packed, row_offsets, elem_offsets, y_packed)
+        X = torch.empty(int(sum(int(m) for m in m_list)), dtype=torch.float64, device=A_packed.device)
+        bt.solution(X)
+        ctx.bt = bt
+        ctx.save_for_backward(A_packed, y_packed, row_offsets, elem_offsets)
+        return X
+
+    @staticmethod
+    def backward(ctx, gX):
+        A, y, ro, eo = ctx.saved_tensors
+        gA = torch.empty_like(A)
+        gy = torch.empty_like(y)
+        ctx.bt.adjoint(A, ro, eo, y, y.numel(), gX.contiguous(), gA, gy)
+        return gA, gy, None, None, None, None, None
+
+
+def lstsq_rg_batch(A_packed, y_packed, row_offsets, elem_offsets, m_list, tol: float = 1e-10,
+                   mode: int = rg.RG_FP64):
+    """X_packed (instances back to back by m_b) for a packed batch (rg_batch_add_rows
+    layout), differentiable in A_packed and y_packed."""
+    return _LstsqRGBatch.apply(A_packed, y_packed, row_offsets, elem_offsets, list(m_list), tol, mode)

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/rg.h"
+#include "rg_adjoint.cuh"
 #include "rg_core.cuh"
 #include "rg_host.h"
 
@@ -290,6 +291,73 @@ __global__ void __launch_bounds__(NT, 2) batch_solution_kernel(BatchDev D, doubl
   }
 }
 
+// Adjoint of every instance's solution (one CTA per instance, strided): w and the
+// Cholesky factor of P (form_w), then adjoint_run with the CTA as the team. Workspace wk:
+// 4 m-vectors per instance at 4 x_off, 7 r_max_max-vectors per instance, 3 n-vectors per
+// instance at 3 row_off.
+__global__ void __launch_bounds__(NT, 2) batch_adjoint_kernel(BatchDev D, const double* __restrict__ Gp,
+                                                              const int64_t* __restrict__ roff,
+                                                              const int64_t* __restrict__ eoff,
+                                                              const double* __restrict__ yp,
+                                                              const double* __restrict__ gp,
+                                                              const int64_t* __restrict__ xoff, double* gAp,
+                                                              double* gyp, double* wk, long long sum_m) {
+  StreamDev S{};
+  scratch_layout(D.kb_max, D.ld_max, D.r_max_max, D.nmc_max,
+                 D.scratch + (size_t)blockIdx.x * D.scratch_stride, &S);
+  double* wm = wk;
+  double* wr = wk + 4 * sum_m;
+  double* wn = wr + (size_t)7 * D.r_max_max * D.B;
+  for (int b = blockIdx.x; b < D.B; b += gridDim.x) {
+    const int m = D.m[b];
+    const long long n = roff[b + 1] - roff[b];
+    if (n < 0 || eoff[b + 1] - eoff[b] != n * (long long)m) {
+      if (threadIdx.x == 0) {
+        atomicOr(D.ctrl + (size_t)b * CTRL_N + CTRL_STATUS, ST_BADARG);
+        atomicOr(D.bstatus, ST_BADARG);
+      }
+      continue;
+    }
+    S.m = m;
+    S.ld = (m + 3) / 4 * 4;
+    S.r_max = D.r_max[b];
+    S.mixed = D.mixed;
+    S.ctrl = D.ctrl + (size_t)b * CTRL_N;
+    inst_layout(m, S.ld, S.r_max, D.mixed, D.state + D.soff[b], &S);
+    const int r = D.ctrl[(size_t)b * CTRL_N + CTRL_R];
+    __syncthreads();
+    form_w(S, r);
+    const long long x0 = xoff ? xoff[b] : D.xoff_def[b];
+    const long long xw = D.xoff_def[b];
+    AdjArgs J{};
+    J.A = Gp + eoff[b];
+    J.y = yp + roff[b];
+    J.n = n;
+    J.g = gp + x0;
+    J.gA = gAp + eoff[b];
+    J.gy = gyp + roff[b];
+    J.X = wm + 4 * xw;
+    J.Aph = J.X + m;
+    J.gperp = J.Aph + m;
+    J.v = J.gperp + m;
+    double* rv = wr + (size_t)7 * D.r_max_max * b;
+    J.a = rv;
+    J.c = rv + D.r_max_max;
+    J.e = rv + 2 * D.r_max_max;
+    J.al = rv + 3 * D.r_max_max;
+    J.be = rv + 4 * D.r_max_max;
+    J.bth = rv + 5 * D.r_max_max;
+    J.de = rv + 6 * D.r_max_max;
+    J.h = wn + 3 * roff[b];
+    J.z = J.h + n;
+    J.rho = J.z + n;
+    J.part = nullptr;
+    J.nrc = 1;
+    adjoint_run<CtaTeam>(CtaTeam{}, S, J, r);
+    __syncthreads();
+  }
+}
+
 __global__ void batch_reset_kernel(BatchDev D, int kb0) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < D.B; b += gridDim.x * blockDim.x) {
     int* c = D.ctrl + (size_t)b * CTRL_N;
@@ -500,6 +568,30 @@ rg_status rg_batch_reset(rg_batch* bt) {
   batch_reset_kernel<<<(bt->D.B + 255) / 256, 256, 0, bt->stream>>>(bt->D, kb0_of(bt->D));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "rg_batch_reset");
+  return RG_OK;
+}
+
+rg_status rg_batch_adjoint(rg_batch* bt, const double* Gamma_packed, const int64_t* row_offsets,
+                           const int64_t* elem_offsets, const double* y_packed, int64_t total_rows,
+                           const double* g_packed, const int64_t* x_offsets, double* gA_packed,
+                           double* gy_packed) {
+  if (!valid_batch(bt)) return fail(RG_EINVAL, "rg_batch_adjoint: invalid batch");
+  if (total_rows < 0) return fail(RG_EINVAL, "rg_batch_adjoint: total_rows < 0");
+  if (!row_offsets || !elem_offsets || !g_packed || (total_rows > 0 && (!Gamma_packed || !y_packed || !gA_packed || !gy_packed)))
+    return fail(RG_EINVAL, "rg_batch_adjoint: NULL buffer");
+  const BatchDev& D = bt->D;
+  long long sum_m = 0;
+  for (int b = 0; b < D.B; ++b) sum_m += bt->m[b];
+  const size_t doubles = (size_t)4 * sum_m + (size_t)7 * D.r_max_max * D.B + (size_t)3 * std::max<int64_t>(total_rows, 1);
+  double* wk = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&wk, doubles * sizeof(double), bt->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_batch_adjoint: workspace");
+  batch_adjoint_kernel<<<bt->grid, NT, 0, bt->stream>>>(D, Gamma_packed, row_offsets, elem_offsets, y_packed,
+                                                        g_packed, x_offsets, gA_packed, gy_packed, wk, sum_m);
+  e = cudaGetLastError();
+  const cudaError_t e2 = cudaFreeAsync(wk, bt->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_batch_adjoint: launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "rg_batch_adjoint: workspace release");
   return RG_OK;
 }
 

@@ -13,6 +13,7 @@
 #include <string>
 
 #include "../../include/rg.h"
+#include "rg_adjoint.cuh"
 #include "rg_host.h"
 #include "rg_internal.cuh"
 
@@ -275,6 +276,55 @@ rg_status rg_solution(rg_state* st, double* X, int64_t* rank_out) {
   cudaError_t e = launch_solution(st->S, X, st->stream);
   if (e != cudaSuccess) return cuda_fail(e, "rg_solution: launch");
   if (rank_out) return rg_rank(st, rank_out);
+  return RG_OK;
+}
+
+rg_status rg_adjoint(rg_state* st, const double* A, const double* y, int64_t n, const double* g,
+                     double* gA, double* gy, double* X) {
+  if (!valid_state(st)) return fail(RG_EINVAL, "rg_adjoint: invalid state");
+  if (n < 0) return fail(RG_EINVAL, "rg_adjoint: n = %lld < 0", (long long)n);
+  if (!g || (n > 0 && (!A || !y || !gA || !gy)))
+    return fail(RG_EINVAL, "rg_adjoint: NULL buffer");
+  const StreamDev& S = st->S;
+  const long long m = S.m, rm = S.r_max;
+  const int nrc = (int)std::max<long long>(1, std::min<long long>(
+      (n + 255) / 256, std::max<long long>(1, 4LL * st->grid / ((m + NT - 1) / NT))));
+  // scratch: X, A^+ h, g_perp, A^T h (m each), seven r_max vectors, h, z, rho (n each),
+  // row-chunk partials (nrc x m)
+  const size_t doubles = (size_t)4 * m + 7 * (size_t)rm + 3 * (size_t)std::max<int64_t>(n, 1) + (size_t)nrc * m;
+  double* wk = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&wk, doubles * sizeof(double), st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_adjoint: workspace");
+  AdjArgs J{};
+  J.A = A;
+  J.y = y;
+  J.n = n;
+  J.g = g;
+  J.gA = gA;
+  J.gy = gy;
+  double* p = wk;
+  J.X = p; p += m;
+  J.Aph = p; p += m;
+  J.gperp = p; p += m;
+  J.v = p; p += m;
+  J.a = p; p += rm;
+  J.c = p; p += rm;
+  J.e = p; p += rm;
+  J.al = p; p += rm;
+  J.be = p; p += rm;
+  J.bth = p; p += rm;
+  J.de = p; p += rm;
+  J.h = p; p += std::max<int64_t>(n, 1);
+  J.z = p; p += std::max<int64_t>(n, 1);
+  J.rho = p; p += std::max<int64_t>(n, 1);
+  J.part = p;
+  J.nrc = nrc;
+  e = launch_solution(S, J.X, st->stream);  // w and the Cholesky factor of P
+  if (e == cudaSuccess) e = launch_adjoint(S, J, st->grid, st->stream);
+  if (e == cudaSuccess && X) e = cudaMemcpyAsync(X, J.X, m * sizeof(double), cudaMemcpyDeviceToDevice, st->stream);
+  const cudaError_t e2 = cudaFreeAsync(wk, st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_adjoint: launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "rg_adjoint: workspace release");
   return RG_OK;
 }
 

@@ -22,5 +22,7 @@ cudaError_t launch_export_prep(const StreamDev& S, int grid, cudaStream_t stream
 cudaError_t launch_solution(const StreamDev& S, double* X, cudaStream_t stream);
 cudaError_t launch_export(const StreamDev& S, double* C, double* Ct, double* Pinv, double* w,
                           long long* basis, cudaStream_t stream);
+struct AdjArgs;
+cudaError_t launch_adjoint(const StreamDev& S, const AdjArgs& J, int grid, cudaStream_t stream);
 
 }  // namespace rg

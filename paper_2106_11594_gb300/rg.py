@@ -65,6 +65,8 @@ def lib(build: bool = True):
         "rg_batch_reset": [vp],
         "rg_batch_free": [vp],
         "rg_solve_noalloc": [vp, vp, i64, i64, f64, i32, i64, vp, vp, vp],
+        "rg_adjoint": [vp, vp, vp, i64, vp, vp, vp, vp],
+        "rg_batch_adjoint": [vp, vp, vp, vp, vp, i64, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -147,6 +149,12 @@ class RankGreville:
                "rg_solution")
         return int(r.value) if with_rank else None
 
+    def adjoint(self, A, y, g, gA, gy, X=None):
+        """rg_adjoint: dL/dA into gA and dL/dy into gy for dL/dX = g, given the rows A and
+        targets y fed since init/reset (float64 CUDA tensors)."""
+        _check(lib().rg_adjoint(self._h, _ptr(A), _ptr(y), int(A.shape[0]), _ptr(g), _ptr(gA),
+                                _ptr(gy), _ptr(X)), "rg_adjoint")
+
     def solution_host(self, X):
         r = ctypes.c_int64(0)
         _check(lib().rg_solution_host(self._h, _ptr(X), ctypes.byref(r)), "rg_solution_host")
@@ -216,6 +224,14 @@ class RankGrevilleBatch:
     def solution(self, X_packed, x_offsets=None, ranks=None):
         _check(lib().rg_batch_solution(self._h, _ptr(X_packed), _ptr(x_offsets), _ptr(ranks)),
                "rg_batch_solution")
+
+    def adjoint(self, Gamma_packed, row_offsets, elem_offsets, y_packed, total_rows, g_packed,
+                gA_packed, gy_packed, x_offsets=None):
+        """rg_batch_adjoint: gradients of every instance (same packing as add_rows)."""
+        _check(lib().rg_batch_adjoint(self._h, _ptr(Gamma_packed), _ptr(row_offsets),
+                                      _ptr(elem_offsets), _ptr(y_packed), int(total_rows),
+                                      _ptr(g_packed), _ptr(x_offsets), _ptr(gA_packed),
+                                      _ptr(gy_packed)), "rg_batch_adjoint")
 
     def sync(self):
         _check(lib().rg_batch_sync(self._h), "rg_batch_sync")
