@@ -240,6 +240,8 @@ def run_gpu(args):
         for mode, mname in ((rg.RG_MIXED, "mixed"), (rg.RG_FP64, "fp64")):
             extra[f"batch_uneven4096_{mname}"] = run_batched("uneven", shapes3, 3, 1e-4, mode, 1, 1, dev, ws, rank)
             extra[f"batch_uniform1024_{mname}"] = run_batched("uniform", shapes4, 4, 1e-3, mode, 1, 1, dev, ws, rank)
+            extra[f"adjoint_uniform1024_{mname}"] = run_batched("uniform", shapes4, 4, 1e-3, mode, 1, 1, dev, ws, rank,
+                                                               backward=True)
     # --- roofline of the dominant kernel (the stream kernel, one launch per 32-row call)
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak = fp64_peak_tflops(sm_mhz)
@@ -296,14 +298,16 @@ def make_batch_on_gpu(shapes, workload_id, noise, dev, ids=None):
     return A, Y, torch.from_numpy(ro).to(dev), torch.from_numpy(eo).to(dev), m
 
 
-def run_batched(name, shapes, workload_id, noise, mode, steps, warmup, dev, ws=1, rank=0):
+def run_batched(name, shapes, workload_id, noise, mode, steps, warmup, dev, ws=1, rank=0, backward=False):
     """Times one batched workload. With several ranks the instances are partitioned by
     LPT on their cost (each rank keeps the seeded draws of its own instance ids) and the
-    rate is all ranks' rows over the slowest rank's time."""
+    rate is all ranks' rows over the slowest rank's time. backward=True times the
+    differentiable form instead: forward, the loss L = sum_b ||X_b - x_target,b||^2 and
+    the adjoint (dL/dA, dL/dy of every instance) per step."""
     import torch
 
     from paper_2106_11594_gb300 import dist as rgdist
-    from paper_2106_11594_gb300 import rg
+    from paper_2106_11594_gb300 import inputs, rg
     ids = np.arange(len(shapes))
     if ws > 1:
         ns, ms_, rs = (np.array([s[i] for s in shapes]) for i in range(3))
@@ -314,11 +318,21 @@ def run_batched(name, shapes, workload_id, noise, mode, steps, warmup, dev, ws=1
     bt = rg.RankGrevilleBatch(m, 1e-10, mode)
     X = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
     ranks = torch.empty(len(shapes), dtype=torch.int64, device=dev)
+    if backward:
+        xt = torch.cat([torch.from_numpy(inputs.rng_for(workload_id, 1 << 20 | int(i)).standard_normal(int(mb)))
+                        for i, mb in zip(ids, m)]).to(dev)
+        gA = torch.empty_like(A)
+        gY = torch.empty_like(Y)
+        gX = torch.empty_like(X)
 
     def step():
         bt.reset()
         bt.add_rows(A, ro, eo, Y)
         bt.solution(X, None, ranks)
+        if backward:
+            torch.sub(X, xt, out=gX)
+            gX.mul_(2.0)
+            bt.adjoint(A, ro, eo, Y, Y.numel(), gX, gA, gY)
 
     for _ in range(warmup):
         step()

@@ -228,6 +228,56 @@ __device__ void phase_gamma(const Team& T, const StreamDev& S, const double* __r
   }
 }
 
+// Small FP64 blocks: the same products with CTA items of 4 rows x 2 basis rows whose
+// columns are split over the 8 warps (warp w takes columns 32 w + lane + 256 k), so that
+// every SM sub-partition has FP64 work even when there are fewer items than warps (one
+// warp per item would leave three of an SM's four FP64 units idle). The 8 partial sums of
+// each lane are combined by a butterfly transpose-reduction, then across the warps in
+// shared memory.
+template <class Team>
+__device__ void phase_gamma_cta(const Team& T, const StreamDev& S, const double* __restrict__ gam,
+                                int row_lo, int row_hi, int r, const double* __restrict__ basis64) {
+  constexpr int NJ = 4, NI = 2, N = NJ * NI;
+  const int nrows = row_hi - row_lo;
+  if (nrows <= 0 || r <= 0) return;
+  const int m = S.m, ld = S.ld, rm = S.r_max;
+  const int nj = (nrows + NJ - 1) / NJ, ni = (r + NI - 1) / NI;
+  const long long nitems = (long long)nj * ni;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ double red[NWARP][N];
+  for (long long it = T.id(); it < nitems; it += T.size()) {
+    const int gj = (int)(it / ni), gi = (int)(it - (long long)gj * ni);
+    const int j0 = row_lo + gj * NJ, i0 = gi * NI;
+    double acc[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) acc[q] = 0.0;
+#pragma unroll 4
+    for (int c = warp * 32 + lane; c < m; c += NT) {
+      double gv[NJ], bv[NI];
+#pragma unroll
+      for (int a = 0; a < NJ; ++a) gv[a] = (j0 + a < row_hi) ? __ldg(gam + (size_t)(j0 + a) * m + c) : 0.0;
+#pragma unroll
+      for (int bb = 0; bb < NI; ++bb) bv[bb] = (i0 + bb < r) ? __ldcg(basis64 + (size_t)(i0 + bb) * ld + c) : 0.0;
+#pragma unroll
+      for (int a = 0; a < NJ; ++a)
+#pragma unroll
+        for (int bb = 0; bb < NI; ++bb) acc[a * NI + bb] = fma(bv[bb], gv[a], acc[a * NI + bb]);
+    }
+    const double tot = warp_transpose_sum<double, N>(acc);
+    const int q = transpose_sum_index<N>();
+    if ((lane & (32 / N - 1)) == 0) red[warp][q] = tot;
+    __syncthreads();
+    if (threadIdx.x < N) {
+      double v = 0.0;
+#pragma unroll
+      for (int w2 = 0; w2 < NWARP; ++w2) v += red[w2][threadIdx.x];
+      const int a = threadIdx.x / NI, bb = threadIdx.x - a * NI;
+      if (j0 + a < row_hi && i0 + bb < r) S.G[(size_t)(j0 + a) * rm + i0 + bb] = v;
+    }
+    __syncthreads();
+  }
+}
+
 // Gamma_r = Gamma_j - B^T gamma_j with B = C (general) or Q (orthonormal). CTA item =
 // (4 RPT rows) x (MC columns): thread (row lane rl, column cc) handles rows rl, rl + 4,
 // ..., so each staged basis tile serves 4 RPT rows. The basis tile (RC ranks x MC
@@ -394,10 +444,11 @@ __device__ void phase_dall(const Team& T, const StreamDev& S, const CallArgs& A,
   const long long wstride = (long long)T.size() * NWARP;
   for (long long j = rr_warp(T); j < b; j += wstride) {
     const double* g = S.G + (size_t)j * S.r_max;
+    const double yv = __ldg(A.y + j0 + j);
     double acc = 0.0;
     for (int l = lane; l < r; l += 32) acc = fma(__ldcg(g + l), __ldcg(S.wb + l), acc);
     acc = warp_sum(acc);
-    if (lane == 0) S.Dall[j] = __ldg(A.y + j0 + j) - acc;
+    if (lane == 0) S.Dall[j] = yv - acc;
   }
 }
 
@@ -425,12 +476,13 @@ __device__ int decide_rows(const StreamDev& S, const CallArgs& A, long long j0, 
   // four rows are issued before the reductions
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int jb = 0; jb < b; jb += 4 * NWARP) {
-    double s4[4], t4[4];
+    double s4[4], t4[4], y4[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = jb + q * NWARP + warp;
       s4[q] = 0.0;
       t4[q] = 0.0;
+      y4[q] = (j < b) ? __ldg(A.y + j0 + j) : 0.0;
       if (j < b)
         for (int c = lane; c < nmc; c += 32) {
           s4[q] += __ldcg(S.spart + (size_t)j * nmc + c);
@@ -447,7 +499,7 @@ __device__ int decide_rows(const StreamDev& S, const CallArgs& A, long long j0, 
           S.s[j] = s;
           S.t[j] = t;
         }
-        const double yv = __ldg(A.y + j0 + j);
+        const double yv = y4[q];
         bool special = !isfinite(t) || !isfinite(yv);
         if (!special) {
           if (MIXED) special = !fp32_screen_dependent(s, t, tc);
@@ -519,9 +571,21 @@ __device__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int
   V* Ds = Gs + (size_t)rows_per * r;
   for (long long base = 0; base < ntot; base += (long long)EMAX * tstride) {
     V acc[EMAX];
+    double old[EMAX];  // current P / u entries, loaded before the products
 #pragma unroll
     for (int q = 0; q < EMAX; ++q) acc[q] = V(0);
     const long long e0 = base + rr_thread(T);
+#pragma unroll
+    for (int q = 0; q < EMAX; ++q) {
+      const long long e = e0 + (long long)q * tstride;
+      old[q] = 0.0;
+      if (e < nP) {
+        const int i = (int)(e / r), l = (int)(e - (long long)i * r);
+        old[q] = __ldcg(S.P + (size_t)i * rm + l);
+      } else if (e < ntot) {
+        old[q] = __ldcg(S.u + (e - nP));
+      }
+    }
     for (int jb = a; jb < a + len; jb += rows_per) {
       const int nr = min(rows_per, a + len - jb);
       if (staged) {
@@ -541,7 +605,7 @@ __device__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int
         const bool isP = e < nP;
         const int i = isP ? (int)(e / r) : (int)(e - nP);
         const int l = isP ? (int)(e - (long long)i * r) : 0;
-        V x0 = V(0), x1 = V(0);
+        V x[4] = {V(0), V(0), V(0), V(0)};  // four independent chains
         for (int jj = 0; jj < nr; ++jj) {
           V gi, gl;
           if (staged) {
@@ -551,10 +615,9 @@ __device__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int
             gi = (V)__ldcg(S.G + (size_t)(jb + jj) * rm + i);
             gl = (V)(isP ? __ldcg(S.G + (size_t)(jb + jj) * rm + l) : __ldcg(S.Dall + jb + jj));
           }
-          if (jj & 1) x1 = fma(gi, gl, x1);
-          else x0 = fma(gi, gl, x0);
+          x[jj & 3] = fma(gi, gl, x[jj & 3]);
         }
-        acc[q] += x0 + x1;
+        acc[q] += (x[0] + x[1]) + (x[2] + x[3]);
       }
     }
 #pragma unroll
@@ -563,11 +626,9 @@ __device__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int
       if (e >= ntot) continue;
       if (e < nP) {
         const int i = (int)(e / r), l = (int)(e - (long long)i * r);
-        const size_t o = (size_t)i * rm + l;
-        S.P[o] = __ldcg(S.P + o) + (double)acc[q];
+        S.P[(size_t)i * rm + l] = old[q] + (double)acc[q];
       } else {
-        const int i = (int)(e - nP);
-        S.u[i] = __ldcg(S.u + i) + (double)acc[q];
+        S.u[e - nP] = old[q] + (double)acc[q];
       }
     }
   }
@@ -1091,10 +1152,10 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
   __shared__ int sh[8];
   long long j0 = 0;
   while (j0 < A.k) {
-    if (threadIdx.x == 0) {
-      sh[0] = ld_acquire_i32(S.ctrl + CTRL_STATUS);
-      sh[1] = ld_acquire_i32(S.ctrl + CTRL_R);
-      sh[2] = ld_acquire_i32(S.ctrl + CTRL_KB);
+    if (threadIdx.x == 0) {  // written before the last barrier or by an earlier launch
+      sh[0] = __ldcg(S.ctrl + CTRL_STATUS);
+      sh[1] = __ldcg(S.ctrl + CTRL_R);
+      sh[2] = __ldcg(S.ctrl + CTRL_KB);
     }
     __syncthreads();
     if (sh[0] != 0) break;
@@ -1125,6 +1186,8 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       const int gr = min(8, (int)((POOL_DOUBLES * 2) / max(S.m, 1)));  // FP32 rows that fit
       if (MIXED && gr >= 1 && (long long)(b / gr) >= 2LL * T.size())
         phase_gamma_f32_staged(T, S, gam, 0, b, r, gr);
+      else if (!MIXED && (long long)((b + 7) / 8) * r < 4LL * NWARP * T.size())
+        phase_gamma_cta(T, S, gam, 0, b, r, S.Ct);  // few warp items: split each over a CTA
       else
         phase_gamma<Team, MIXED>(T, S, gam, 0, b, r, MIXED ? S.C : S.Ct);
       if (!T.sync()) return false;
@@ -1154,7 +1217,7 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       } else {
         decide_rows_team<Team, MIXED>(T, S, A, j0, b, r);
         if (!T.sync()) return false;
-        if (threadIdx.x == 0) sh[3] = ld_acquire_i32(S.ctrl + CTRL_Q0);
+        if (threadIdx.x == 0) sh[3] = __ldcg(S.ctrl + CTRL_Q0);
         __syncthreads();
         q0 = sh[3];
       }
@@ -1165,16 +1228,19 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
     if (q0 < b) {
       // 5: sequential section, in FP64 (rows [q0, bend)); its rows never overlap the run
       const int bend = min(b, q0 + SLOW_MAX);
-      phase_gamma<Team, false>(T, S, gam, q0, bend, r, MIXED ? S.C : S.Ct);
+      if ((long long)((bend - q0 + 7) / 8) * r < 4LL * NWARP * T.size())
+        phase_gamma_cta(T, S, gam, q0, bend, r, MIXED ? S.C : S.Ct);
+      else
+        phase_gamma<Team, false>(T, S, gam, q0, bend, r, MIXED ? S.C : S.Ct);
       if (!T.sync()) return false;
       phase_reject<Team, false, 1>(T, S, gam, q0, bend, r, S.C, S.R);
       if (!T.sync()) return false;
       if (!scan_team<Team, MIXED>(T, S, A, j0, q0, bend, r)) return false;
       if (!T.sync()) return false;
       if (threadIdx.x == 0) {
-        sh[5] = ld_acquire_i32(S.ctrl + CTRL_APPLIED);
-        sh[6] = ld_acquire_i32(S.ctrl + CTRL_RNEW);
-        sh[7] = ld_acquire_i32(S.ctrl + CTRL_NIND);
+        sh[5] = __ldcg(S.ctrl + CTRL_APPLIED);  // published before the barrier above
+        sh[6] = __ldcg(S.ctrl + CTRL_RNEW);
+        sh[7] = __ldcg(S.ctrl + CTRL_NIND);
       }
       __syncthreads();
       applied = sh[5];

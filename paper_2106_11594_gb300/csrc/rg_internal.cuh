@@ -150,23 +150,17 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsig
 }
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident), on a monotonic 64-bit
-// arrival counter (control words CTRL_BAR_COUNT..+1): each CTA adds 1 with a release
-// reduction and waits, with acquire loads, until the counter reaches its next multiple of
-// gridDim.x. grid_barrier_init() must run once per launch before the first barrier; it
-// rounds the counter down to a multiple of gridDim.x (no CTA can have completed a barrier
-// of this launch yet, so at most gridDim.x - 1 early arrivals are rounded away).
+// arrival counter (control words CTRL_BAR_COUNT..+1) that is a multiple of gridDim.x
+// between barriers: each CTA adds 1 with an atomic that returns the old value, which
+// fixes the barrier's target ((old / gridDim.x + 1) gridDim.x: no CTA can arrive at the
+// next barrier before this one completes), and waits with acquire loads until the counter
+// reaches it. No per-launch initialisation is needed.
 // The wait is bounded: after WAIT_LIMIT_NS the CTA records ST_TIMEOUT and returns false.
-__device__ __forceinline__ unsigned long long& grid_barrier_target() {
-  __shared__ unsigned long long target;
-  return target;
-}
-__device__ __forceinline__ void grid_barrier_init(int* ctrl) {
-  if (threadIdx.x == 0) {
-    const unsigned long long c =
-        ld_acquire_u64(reinterpret_cast<unsigned long long*>(ctrl + CTRL_BAR_COUNT));
-    grid_barrier_target() = (c / gridDim.x) * gridDim.x;
-  }
-  __syncthreads();
+__device__ __forceinline__ void grid_barrier_init(int* /*ctrl*/) {}
+__device__ __forceinline__ unsigned long long atom_release_add_u64(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
 }
 __device__ __forceinline__ bool grid_barrier(int* ctrl) {
   __shared__ int ok;
@@ -174,9 +168,8 @@ __device__ __forceinline__ bool grid_barrier(int* ctrl) {
   if (threadIdx.x == 0) {
     ok = 1;
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ctrl + CTRL_BAR_COUNT);
-    const unsigned long long target = grid_barrier_target() + gridDim.x;
-    grid_barrier_target() = target;
-    red_release_add_u64(cnt, 1ull);
+    const unsigned long long old = atom_release_add_u64(cnt, 1ull);
+    const unsigned long long target = (old / gridDim.x + 1) * gridDim.x;
     if (ld_acquire_u64(cnt) < target) {
       const unsigned long long t0 = global_ns();
       while (ld_acquire_u64(cnt) < target) {
