@@ -38,6 +38,27 @@ METRIC = ("row updates/sec (device-timed, batched & single) at stated rel. error
 WORKLOAD = f"single FP64 stream n={N_ROWS} m={M} r={R}, k={K_CALL} rows per rg_add_rows call"
 
 
+# DRAM bytes (read + write) of one 32-row stream_kernel<false> launch, from the ncu capture
+# summarised in profiles/stream_kernel_fp64_k32_n4096_full.md, and the hash of the kernel
+# sources it was taken on: once the sources change the figure no longer applies (null).
+TRAFFIC_BYTES_PER_LAUNCH = 1456896
+TRAFFIC_SOURCES_SHA = "3886d6b04ddff987"
+
+
+def kernel_sources_sha() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2106_11594_gb300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    return TRAFFIC_BYTES_PER_LAUNCH if kernel_sources_sha() == TRAFFIC_SOURCES_SHA else None
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -247,7 +268,7 @@ def run_gpu(args):
     peak = fp64_peak_tflops(sm_mhz)
     achieved = K_CALL * flops_per_row(M, R) / (launch_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": measured_traffic(),
                 "peak_source": f"FP64 vector peak derived: 152 SMs x 4 flop/clk x {sm_mhz:.0f} MHz "
                                "(median SM clock sampled during the timed region)",
                 "kernel": "rg::stream_kernel<false> (one launch per 32-row call)",
