@@ -42,16 +42,19 @@ WORKLOAD = f"single FP64 stream n={N_ROWS} m={M} r={R}, k={K_CALL} rows per rg_a
 # summarised in profiles/stream_kernel_fp64_k32_n4096_full.md, and the hash of the kernel
 # sources it was taken on: once the sources change the figure no longer applies (null).
 TRAFFIC_BYTES_PER_LAUNCH = 1456896
-TRAFFIC_SOURCES_SHA = "3886d6b04ddff987"
+TRAFFIC_SOURCES_SHA = "8b5de691201869df"
+
+
+STREAM_KERNEL_SOURCES = ("rg_stream.cu", "rg_core.cuh", "rg_internal.cuh", "rg_tc.cuh")
 
 
 def kernel_sources_sha() -> str:
-    import glob
+    """Hash of the sources compiled into stream_kernel."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2106_11594_gb300", "csrc", "*"))):
-        h.update(os.path.basename(f).encode())
-        h.update(open(f, "rb").read())
+    for f in STREAM_KERNEL_SOURCES:
+        h.update(f.encode())
+        h.update(open(os.path.join(ROOT, "paper_2106_11594_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -259,9 +262,9 @@ def run_gpu(args):
         shapes3 = [(int(a), int(b), int(c)) for a, b, c in zip(n3, m3, r3)]
         shapes4 = [(2048, 256, 32)] * 1024
         for mode, mname in ((rg.RG_MIXED, "mixed"), (rg.RG_FP64, "fp64")):
-            extra[f"batch_uneven4096_{mname}"] = run_batched("uneven", shapes3, 3, 1e-4, mode, 1, 1, dev, ws, rank)
-            extra[f"batch_uniform1024_{mname}"] = run_batched("uniform", shapes4, 4, 1e-3, mode, 1, 1, dev, ws, rank)
-            extra[f"adjoint_uniform1024_{mname}"] = run_batched("uniform", shapes4, 4, 1e-3, mode, 1, 1, dev, ws, rank,
+            extra[f"batch_uneven4096_{mname}"] = run_batched("uneven", shapes3, 3, 1e-4, mode, 2, 1, dev, ws, rank)
+            extra[f"batch_uniform1024_{mname}"] = run_batched("uniform", shapes4, 4, 1e-3, mode, 2, 1, dev, ws, rank)
+            extra[f"adjoint_uniform1024_{mname}"] = run_batched("uniform", shapes4, 4, 1e-3, mode, 2, 1, dev, ws, rank,
                                                                backward=True)
     # --- roofline of the dominant kernel (the stream kernel, one launch per 32-row call)
     sm_mhz = clocks.get("sm_mhz") or 2070.0
@@ -355,17 +358,38 @@ def run_batched(name, shapes, workload_id, noise, mode, steps, warmup, dev, ws=1
             gX.mul_(2.0)
             bt.adjoint(A, ro, eo, Y, Y.numel(), gX, gA, gY)
 
-    for _ in range(warmup):
-        step()
-    bt.sync()
-    stream = torch.cuda.current_stream()
+    # autotune the per-block row cap on this batch (outside the timed region)
+    from paper_2106_11594_gb300 import autotune
+    kb, kb_times = autotune.tune_block_rows(bt, A, ro, eo, Y, X)
+    # capture one step into a CUDA graph on a side stream and replay it
+    graph = None
+    cap_stream = torch.cuda.Stream()
+    cap_stream.wait_stream(torch.cuda.current_stream())
+    bt.set_stream(cap_stream)
+    with torch.cuda.stream(cap_stream):
+        for _ in range(warmup):
+            step()
+    cap_stream.synchronize()
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap_stream):
+            step()
+        graph = g
+    except Exception as exc:  # capture unsupported here: time direct launches instead
+        print(f"[bench] graph capture failed ({exc}); timing direct launches", file=sys.stderr)
+        torch.cuda.synchronize()
+    stream = cap_stream
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    t0.record(stream)
-    for _ in range(steps):
-        step()
-    t1.record(stream)
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        for _ in range(steps):
+            if graph is not None:
+                graph.replay()
+            else:
+                step()
+        t1.record(stream)
     torch.cuda.synchronize()
     bt.sync()
     ms = t0.elapsed_time(t1) / steps
@@ -375,7 +399,9 @@ def run_batched(name, shapes, workload_id, noise, mode, steps, warmup, dev, ws=1
     rate, ms, rows = rgdist.job_throughput(rows_mine, ms, dev)
     match = rgdist.sum_over_ranks(float((rk == expect).sum()), dev)
     out = {"rows_per_s": rate, "ms_per_step": ms, "rows": int(rows),
-           "instances": len(all_shapes), "rank_match_generator": int(match)}
+           "instances": len(all_shapes), "rank_match_generator": int(match),
+           "cuda_graph": graph is not None, "block_rows": kb,
+           "autotune_ms": {str(k): round(v, 3) for k, v in kb_times.items()}}
     bt.close()
     del A, Y
     torch.cuda.empty_cache()

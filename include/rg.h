@@ -217,6 +217,20 @@ rg_status rg_batch_adjoint(rg_batch* bt, const double* Gamma_packed, const int64
                            const double* g_packed, const int64_t* x_offsets, double* gA_packed,
                            double* gy_packed);
 
+/* rg_batch_set_stream -- issue later batch calls on cuda_stream (synchronises the old
+ * stream first). Lets a caller capture the batch calls into a CUDA graph. */
+rg_status rg_batch_set_stream(rg_batch* bt, void* cuda_stream);
+
+/*
+ * rg_batch_set_block_rows -- cap on the rows an instance takes per internal block (the
+ * block grows from 64 rows after a rank change up to this cap while rows stay dependent;
+ * Section 3's block of observations). rows > 0 sets it (32 <= rows <= the capacity laid
+ * out at init, which depends on the largest r_max; otherwise RG_EINVAL); rows <= 0 only
+ * queries. rows_out (host, may be NULL) receives the cap in force. Host-side only; takes
+ * effect at the next rg_batch_add_rows. Used by the autotuner.
+ */
+rg_status rg_batch_set_block_rows(rg_batch* bt, int64_t rows, int64_t* rows_out);
+
 /* rg_batch_sync -- wait and return any pending device error of the batch. */
 rg_status rg_batch_sync(rg_batch* bt);
 

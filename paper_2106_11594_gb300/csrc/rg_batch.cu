@@ -24,6 +24,7 @@ namespace rg {
 
 struct BatchDev {
   int B, mixed, test_mode, kb_max, ld_max, r_max_max, nmc_max;
+  int kb_cap;  // rows of block scratch laid out per CTA (kb_max <= kb_cap)
   double tol, tau_lo;
   const int* m;               // B
   const int* r_max;           // B
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, co
   S.tol = D.tol;
   S.tau_lo = D.tau_lo;
   S.kb_max = D.kb_max;
-  scratch_layout(D.kb_max, D.ld_max, D.r_max_max, D.nmc_max,
+  scratch_layout(D.kb_cap, D.ld_max, D.r_max_max, D.nmc_max,
                  D.scratch + (size_t)blockIdx.x * D.scratch_stride, &S);
   for (;;) {
     if (threadIdx.x == 0) item = atomicAdd(D.queue, 1);
@@ -267,7 +268,7 @@ __global__ void order_kernel(BatchDev D, const int64_t* __restrict__ roff) {
 __global__ void __launch_bounds__(NT, 2) batch_solution_kernel(BatchDev D, double* X, const int64_t* xoff,
                                                               int64_t* ranks) {
   StreamDev S{};
-  scratch_layout(D.kb_max, D.ld_max, D.r_max_max, D.nmc_max,
+  scratch_layout(D.kb_cap, D.ld_max, D.r_max_max, D.nmc_max,
                  D.scratch + (size_t)blockIdx.x * D.scratch_stride, &S);
   for (int b = blockIdx.x; b < D.B; b += gridDim.x) {
     const int m = D.m[b];
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(NT, 2) batch_adjoint_kernel(BatchDev D, const 
                                                               const int64_t* __restrict__ xoff, double* gAp,
                                                               double* gyp, double* wk, long long sum_m) {
   StreamDev S{};
-  scratch_layout(D.kb_max, D.ld_max, D.r_max_max, D.nmc_max,
+  scratch_layout(D.kb_cap, D.ld_max, D.r_max_max, D.nmc_max,
                  D.scratch + (size_t)blockIdx.x * D.scratch_stride, &S);
   double* wm = wk;
   double* wr = wk + 4 * sum_m;
@@ -434,9 +435,10 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
   D.ld_max = (mmax + 3) / 4 * 4;
   D.r_max_max = rmm;
   D.nmc_max = (mmax + MC - 1) / MC;
-  int kb = 256;
-  while (kb > 32 && (size_t)kb * rmm * 8 > (size_t)2 << 20) kb /= 2;
-  D.kb_max = kb;
+  int kb = 512;  // layout capacity; the default block cap is 256 (rg_batch_set_block_rows)
+  while (kb > 32 && (size_t)kb * rmm * 8 > (size_t)4 << 20) kb /= 2;
+  D.kb_cap = kb;
+  D.kb_max = std::min(kb, 256);
   int nsm = 0, per = 0;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, bt->device);
   if (e == cudaSuccess)
@@ -464,7 +466,7 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
     xoff[b + 1] = xoff[b] + bt->m[b];
   }
   StreamDev tmp{};
-  D.scratch_stride = al256(scratch_layout(D.kb_max, D.ld_max, D.r_max_max, D.nmc_max, nullptr, &tmp));
+  D.scratch_stride = al256(scratch_layout(D.kb_cap, D.ld_max, D.r_max_max, D.nmc_max, nullptr, &tmp));
   size_t off = 0;
   auto place = [&](size_t bytes) {
     const size_t o = off;
@@ -592,6 +594,25 @@ rg_status rg_batch_adjoint(rg_batch* bt, const double* Gamma_packed, const int64
   const cudaError_t e2 = cudaFreeAsync(wk, bt->stream);
   if (e != cudaSuccess) return cuda_fail(e, "rg_batch_adjoint: launch");
   if (e2 != cudaSuccess) return cuda_fail(e2, "rg_batch_adjoint: workspace release");
+  return RG_OK;
+}
+
+rg_status rg_batch_set_stream(rg_batch* bt, void* cuda_stream) {
+  if (!valid_batch(bt)) return fail(RG_EINVAL, "rg_batch_set_stream: invalid batch");
+  cudaError_t e = cudaStreamSynchronize(bt->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_batch_set_stream");
+  bt->stream = (cudaStream_t)cuda_stream;
+  return RG_OK;
+}
+
+rg_status rg_batch_set_block_rows(rg_batch* bt, int64_t rows, int64_t* rows_out) {
+  if (!valid_batch(bt)) return fail(RG_EINVAL, "rg_batch_set_block_rows: invalid batch");
+  if (rows > 0) {
+    if (rows < 32 || rows > bt->D.kb_cap)
+      return fail(RG_EINVAL, "rg_batch_set_block_rows: %lld outside [32, %d]", (long long)rows, bt->D.kb_cap);
+    bt->D.kb_max = (int)rows;
+  }
+  if (rows_out) *rows_out = bt->D.kb_max;
   return RG_OK;
 }
 

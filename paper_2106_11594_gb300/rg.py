@@ -67,6 +67,8 @@ def lib(build: bool = True):
         "rg_solve_noalloc": [vp, vp, i64, i64, f64, i32, i64, vp, vp, vp],
         "rg_adjoint": [vp, vp, vp, i64, vp, vp, vp, vp],
         "rg_batch_adjoint": [vp, vp, vp, vp, vp, i64, vp, vp, vp, vp],
+        "rg_batch_set_stream": [vp, vp],
+        "rg_batch_set_block_rows": [vp, i64, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -232,6 +234,18 @@ class RankGrevilleBatch:
                                       _ptr(elem_offsets), _ptr(y_packed), int(total_rows),
                                       _ptr(g_packed), _ptr(x_offsets), _ptr(gA_packed),
                                       _ptr(gy_packed)), "rg_batch_adjoint")
+
+    def set_stream(self, stream=None):
+        """Issue later calls on `stream` (default: torch's current stream), e.g. inside
+        torch.cuda.graph capture."""
+        _check(lib().rg_batch_set_stream(self._h, _stream(stream)), "rg_batch_set_stream")
+
+    def block_rows(self, rows: int = 0) -> int:
+        """Set (rows > 0) and/or return the per-block row cap (rg_batch_set_block_rows)."""
+        out = ctypes.c_int64(0)
+        _check(lib().rg_batch_set_block_rows(self._h, int(rows), ctypes.byref(out)),
+               "rg_batch_set_block_rows")
+        return int(out.value)
 
     def sync(self):
         _check(lib().rg_batch_sync(self._h), "rg_batch_sync")

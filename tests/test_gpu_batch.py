@@ -121,3 +121,60 @@ def test_batch_reset_rerun_identical():
     g1 = run_batch(batch, mode=rg.RG_MIXED)
     g2 = run_batch(batch, mode=rg.RG_MIXED)
     np.testing.assert_array_equal(g1["X"], g2["X"])
+
+
+def test_cuda_graph_replay_matches_direct_calls():
+    """reset + add_rows + solution captured into one CUDA graph (rg_batch_set_stream to
+    the capture stream) and replayed twice give the same X as direct calls, bit for bit."""
+    torch, dev = torch_cuda()
+    batch = inputs.uniform_batch(1024, instances=range(6))
+    A, Y, ro, eo = (torch.from_numpy(a).to(dev) for a in batch.packed()[:4])
+    m = np.array([s.m for s in batch.streams], dtype=np.int64)
+    bt = rg.RankGrevilleBatch(m, 1e-10, rg.RG_MIXED)
+    X1 = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+    X2 = torch.empty_like(X1)
+    bt.reset()
+    bt.add_rows(A, ro, eo, Y)
+    bt.solution(X1)
+    bt.sync()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    bt.set_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        bt.reset()
+        bt.add_rows(A, ro, eo, Y)
+        bt.solution(X2)
+    for _ in range(2):
+        X2.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(X1, X2)
+    bt.sync()
+    bt.close()
+
+
+def test_block_rows_cap():
+    torch, dev = torch_cuda()
+    batch = inputs.uniform_batch(1024, instances=range(4))
+    ores = oracle_batch(batch)
+    m = np.array([s.m for s in batch.streams], dtype=np.int64)
+    bt = rg.RankGrevilleBatch(m, 1e-10, rg.RG_FP64)
+    cap0 = bt.block_rows()
+    assert 32 <= cap0
+    with pytest.raises(rg.RGError):
+        bt.block_rows(16)
+    A, Y, ro, eo = (torch.from_numpy(a).to(dev) for a in batch.packed()[:4])
+    for kb in (64, 128):
+        assert bt.block_rows(kb) == kb
+        X = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+        ranks = torch.empty(len(m), dtype=torch.int64, device=dev)
+        bt.reset()
+        bt.add_rows(A, ro, eo, Y)
+        bt.solution(X, None, ranks)
+        bt.sync()
+        xo = np.concatenate([[0], np.cumsum(m)])
+        for b, o in enumerate(ores):
+            assert int(ranks[b]) == o.rank
+            assert checks.rel_err(X.cpu().numpy()[xo[b]:xo[b + 1]], o.X) <= 1e-10
+    bt.close()
