@@ -472,34 +472,39 @@ __device__ int decide_rows(const StreamDev& S, const CallArgs& A, long long j0, 
   const int nmc = S.nmc;
   double tc = S.tau_lo;
   if (MIXED && S.test_mode == 0 && S.tol > 0.0) tc = fmax(tc, 0.5 * S.tol);
-  // a warp sums the chunk partials of rows warp, warp + NWARP, ...; all loads of up to
-  // four rows are issued before the reductions
+  // a warp takes rows warp, warp + NWARP, warp + 2 NWARP, warp + 3 NWARP of each group of
+  // 4 NWARP rows; all loads are issued first, then one butterfly transpose-reduction sums
+  // the 8 values (s and t of 4 rows) across the lanes (chunks) and lane group p decides
+  // row p / 2
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int jb = 0; jb < b; jb += 4 * NWARP) {
-    double s4[4], t4[4], y4[4];
+    double v[8], y4[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = jb + q * NWARP + warp;
-      s4[q] = 0.0;
-      t4[q] = 0.0;
+      v[2 * q] = 0.0;
+      v[2 * q + 1] = 0.0;
       y4[q] = (j < b) ? __ldg(A.y + j0 + j) : 0.0;
       if (j < b)
         for (int c = lane; c < nmc; c += 32) {
-          s4[q] += __ldcg(S.spart + (size_t)j * nmc + c);
-          t4[q] += __ldcg(S.tpart + (size_t)j * nmc + c);
+          v[2 * q] += __ldcg(S.spart + (size_t)j * nmc + c);
+          v[2 * q + 1] += __ldcg(S.tpart + (size_t)j * nmc + c);
         }
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    const double tot8 = warp_transpose_sum<double, 8>(v);
+    const int idx = transpose_sum_index<8>();  // value index held by this lane
+    // pair (s, t) of row q sits in value indices 2q, 2q + 1: fetch t from the partner lane
+    const double other = __shfl_xor_sync(0xffffffffu, tot8, 32 / 8 * 1);
+    if ((idx & 1) == 0 && (lane & (32 / 8 - 1)) == 0) {
+      const int q = idx >> 1;
       const int j = jb + q * NWARP + warp;
-      const double s = warp_sum(s4[q]);
-      const double t = warp_sum(t4[q]);
-      if (lane == 0 && j < b) {
+      if (j < b) {
+        const double s = tot8, t = other;
         if (publish) {
           S.s[j] = s;
           S.t[j] = t;
         }
-        const double yv = y4[q];
+        const double yv = (q == 0) ? y4[0] : (q == 1) ? y4[1] : (q == 2) ? y4[2] : y4[3];
         bool special = !isfinite(t) || !isfinite(yv);
         if (!special) {
           if (MIXED) special = !fp32_screen_dependent(s, t, tc);
@@ -558,10 +563,13 @@ __device__ void decide_rows_team(const Team& T, const StreamDev& S, const CallAr
 // staged in shared memory in row chunks. Ranks whose gamma rows do not fit the pool read
 // G from L2 directly.
 template <class Team, bool F32>
-__device__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int r) {
+__device__ void acc_rows(const Team& T, const StreamDev& S, const double* Gsrc, const double* Dsrc, int a,
+                         int len, int r, int w_lo) {
   using V = typename std::conditional<F32, float, double>::type;
   const int rm = S.r_max;
-  const long long tstride = (long long)T.size() * NT;
+  if (T.id() < w_lo) return;  // workers [w_lo, size) take part
+  const int nw = T.size() - w_lo;
+  const long long tstride = (long long)nw * NT;
   const long long nP = (long long)r * r, ntot = nP + r;
   constexpr int EMAX = 4;
   constexpr int POOL_V = POOL_DOUBLES * (int)(sizeof(double) / sizeof(V));
@@ -574,7 +582,7 @@ __device__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int
     double old[EMAX];  // current P / u entries, loaded before the products
 #pragma unroll
     for (int q = 0; q < EMAX; ++q) acc[q] = V(0);
-    const long long e0 = base + rr_thread(T);
+    const long long e0 = base + (long long)threadIdx.x * nw + (T.id() - w_lo);
 #pragma unroll
     for (int q = 0; q < EMAX; ++q) {
       const long long e = e0 + (long long)q * tstride;
@@ -593,9 +601,9 @@ __device__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int
 #pragma unroll 8
         for (int e = threadIdx.x; e < nr * r; e += NT) {
           const int jj = e / r, i = e - jj * r;
-          Gs[e] = (V)__ldcg(S.G + (size_t)(jb + jj) * rm + i);
+          Gs[e] = (V)__ldcg(Gsrc + (size_t)(jb + jj) * rm + i);
         }
-        for (int e = threadIdx.x; e < nr; e += NT) Ds[e] = (V)__ldcg(S.Dall + jb + e);
+        for (int e = threadIdx.x; e < nr; e += NT) Ds[e] = (V)__ldcg(Dsrc + jb + e);
         __syncthreads();
       }
 #pragma unroll
@@ -605,19 +613,27 @@ __device__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int
         const bool isP = e < nP;
         const int i = isP ? (int)(e / r) : (int)(e - nP);
         const int l = isP ? (int)(e - (long long)i * r) : 0;
-        V x[4] = {V(0), V(0), V(0), V(0)};  // four independent chains
-        for (int jj = 0; jj < nr; ++jj) {
+        V x0 = V(0), x1 = V(0), x2 = V(0), x3 = V(0);  // four independent chains
+        auto gterm = [&](int jj) -> V {
           V gi, gl;
           if (staged) {
             gi = Gs[jj * r + i];
             gl = isP ? Gs[jj * r + l] : Ds[jj];
           } else {
-            gi = (V)__ldcg(S.G + (size_t)(jb + jj) * rm + i);
-            gl = (V)(isP ? __ldcg(S.G + (size_t)(jb + jj) * rm + l) : __ldcg(S.Dall + jb + jj));
+            gi = (V)__ldcg(Gsrc + (size_t)(jb + jj) * rm + i);
+            gl = (V)(isP ? __ldcg(Gsrc + (size_t)(jb + jj) * rm + l) : __ldcg(Dsrc + jb + jj));
           }
-          x[jj & 3] = fma(gi, gl, x[jj & 3]);
+          return gi * gl;
+        };
+        int jj = 0;
+        for (; jj + 3 < nr; jj += 4) {
+          x0 += gterm(jj);
+          x1 += gterm(jj + 1);
+          x2 += gterm(jj + 2);
+          x3 += gterm(jj + 3);
         }
-        acc[q] += (x[0] + x[1]) + (x[2] + x[3]);
+        for (; jj < nr; ++jj) x0 += gterm(jj);
+        acc[q] += (x0 + x1) + (x2 + x3);
       }
     }
 #pragma unroll
@@ -703,6 +719,11 @@ __device__ void gram_reduce(const Team& T, const StreamDev& S, int r, int nch) {
       S.u[i] = __ldcg(S.u + i) + acc;
     }
   }
+}
+
+template <class Team, bool F32>
+__device__ __forceinline__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int r) {
+  acc_rows<Team, F32>(T, S, S.G, S.Dall, a, len, r, 0);
 }
 
 // A run of dependent rows [a, a + len): short runs directly, long runs through chunked
@@ -1156,6 +1177,7 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       sh[0] = __ldcg(S.ctrl + CTRL_STATUS);
       sh[1] = __ldcg(S.ctrl + CTRL_R);
       sh[2] = __ldcg(S.ctrl + CTRL_KB);
+      sh[4] = S.Gpend ? __ldcg(S.ctrl + CTRL_PEND_ROWS) : 0;
     }
     __syncthreads();
     if (sh[0] != 0) break;
@@ -1195,12 +1217,18 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       if (big_rej) phase_reject<Team, MIXED, 8>(T, S, gam, 0, b, r, S.C, nullptr);
       else phase_reject<Team, MIXED, 1>(T, S, gam, 0, b, r, S.C, nullptr);
       phase_dall(T, S, A, j0, b, r);
+      if (sh[4] > 0) {  // the previous call's deferred P/u update, on the idle CTAs
+        const long long nrej = (long long)((b + 4 * (big_rej ? 8 : 1) - 1) / (4 * (big_rej ? 8 : 1))) * S.nmc;
+        const int w_lo = (int)min(nrej, (long long)max(0, T.size() - 16));
+        acc_rows<Team, MIXED>(T, S, S.Gpend, S.Dpend, 0, sh[4], r, w_lo);
+      }
       if (!T.sync()) return false;
       // 3: decide
       if (b <= SMALL_B) {
         q0 = decide_rows<MIXED>(S, A, j0, b, r, T.id() == 0);
         if (q0 == b) {  // fast finish: every row dependent
-          acc_small<Team, MIXED>(T, S, 0, b, r);
+          const bool defer = S.defer && last && j0 == 0;  // the call's only block
+          if (!defer) acc_small<Team, MIXED>(T, S, 0, b, r);
           if (T.id() == 0) {
             if (A.indep)
               for (int j = threadIdx.x; j < b; j += NT) A.indep[j0 + j] = 0;
@@ -1208,6 +1236,7 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
               *S.rows_seen = __ldcg(S.rows_seen) + b;
               S.ctrl[CTRL_KB] = min(2 * kb0, S.kb_max);
               S.ctrl[CTRL_PEND] = 1;
+              S.ctrl[CTRL_PEND_ROWS] = defer ? b : 0;
             }
           }
           if (!last && !T.sync()) return false;
@@ -1259,6 +1288,7 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
         S.ctrl[CTRL_R] = rnew;
         S.ctrl[CTRL_KB] = (q0 < b) ? min(KB_MIN, S.kb_max) : min(2 * kb0, S.kb_max);
         S.ctrl[CTRL_PEND] = 1;
+        S.ctrl[CTRL_PEND_ROWS] = 0;
       }
     }
     if (!T.sync()) return false;

@@ -80,6 +80,11 @@ struct rg_state {
   uint8_t* stage_ind = nullptr;
   long long stage_rows = 0;
   double* xbuf = nullptr;
+  // two small (SMALL_B-row) gamma / a-priori-error buffers used alternately by calls of at
+  // most SMALL_B rows, so that one call's deferred P/u update survives into the next
+  double* Gs[2] = {nullptr, nullptr};
+  double* Ds[2] = {nullptr, nullptr};
+  int last_small = 1;  // buffer of the most recent small call
 };
 
 namespace {
@@ -99,7 +104,7 @@ struct Carver {
 };
 
 // Lays out every device buffer of a stream; with base == nullptr it only measures.
-size_t carve(StreamDev& S, char* base) {
+size_t carve(StreamDev& S, char* base, double** gs = nullptr, double** ds = nullptr) {
   Carver cv{base};
   const size_t ld = (size_t)S.ld, rm = (size_t)S.r_max, kb = (size_t)S.kb_max;
   S.C = cv.take<double>(rm * ld);
@@ -133,10 +138,46 @@ size_t carve(StreamDev& S, char* base) {
   S.rs_cap = 0;
   S.sp_stride = (size_t)32 * std::min<size_t>((ld + 31) / 32, 1024);  // <= 1024 workers
   S.Sp = cv.take<double>(2 * S.sp_stride);
+  for (int h = 0; h < 2; ++h) {
+    double* g = cv.take<double>((size_t)SMALL_B * rm);
+    double* d = cv.take<double>((size_t)SMALL_B);
+    if (gs) gs[h] = g;
+    if (ds) ds[h] = d;
+  }
   return align_up(cv.off, 256);
 }
 
 bool valid_state(rg_state* st) { return st != nullptr && st->arena != nullptr; }
+
+// The state as one rg_add_rows call of k rows sees it: calls of at most SMALL_B rows use
+// the two small buffers alternately (and may defer their P/u update), larger calls the
+// main block scratch; both fold a pending update left by the previous small call.
+StreamDev call_view(rg_state* st, long long k) {
+  StreamDev S = st->S;
+  if (k <= SMALL_B) {
+    const int h = 1 - st->last_small;
+    S.G = st->Gs[h];
+    S.Dall = st->Ds[h];
+    S.Gpend = st->Gs[1 - h];
+    S.Dpend = st->Ds[1 - h];
+    S.defer = 1;
+    st->last_small = h;
+  } else {
+    S.Gpend = st->Gs[st->last_small];
+    S.Dpend = st->Ds[st->last_small];
+    S.defer = 0;
+  }
+  return S;
+}
+
+// The view for rg_solution / rg_export / rg_adjoint: pending rows of the last small call.
+StreamDev flush_view(rg_state* st) {
+  StreamDev S = st->S;
+  S.Gpend = st->Gs[st->last_small];
+  S.Dpend = st->Ds[st->last_small];
+  S.defer = 0;
+  return S;
+}
 
 rg_status pending_status(rg_state* st, bool clear) {
   int bits = 0;
@@ -199,7 +240,7 @@ rg_status rg_init(rg_state** out, int64_t m, double tol, int flags, int64_t r_ma
     delete st;
     return cuda_fail(e, "rg_init: cudaMalloc of the state");
   }
-  carve(S, (char*)st->arena);
+  carve(S, (char*)st->arena, st->Gs, st->Ds);
   e = stream_grid_size(S.mixed, &st->grid);
   if (e != cudaSuccess || st->grid <= 0) {
     cudaFree(st->arena);
@@ -229,7 +270,7 @@ rg_status rg_add_rows(rg_state* st, const double* Gamma, const double* y, int64_
   if (!Gamma || !y) return fail(RG_EINVAL, "rg_add_rows: NULL rows or targets");
   cudaError_t e = cudaSuccess;
   if (indep_out) e = cudaMemsetAsync(indep_out, 0xFF, (size_t)k, st->stream);
-  if (e == cudaSuccess) e = launch_stream(st->S, Gamma, y, k, indep_out, st->grid, st->stream);
+  if (e == cudaSuccess) e = launch_stream(call_view(st, k), Gamma, y, k, indep_out, st->grid, st->stream);
   if (e != cudaSuccess) return cuda_fail(e, "rg_add_rows: launch");
   return RG_OK;
 }
@@ -273,7 +314,8 @@ rg_status rg_add_rows_host(rg_state* st, const double* Gamma, const double* y, i
 rg_status rg_solution(rg_state* st, double* X, int64_t* rank_out) {
   if (!valid_state(st)) return fail(RG_EINVAL, "rg_solution: invalid state");
   if (!X) return fail(RG_EINVAL, "rg_solution: X is NULL");
-  cudaError_t e = launch_solution(st->S, X, st->stream);
+  cudaError_t e = launch_flush(flush_view(st), st->grid, st->stream);
+  if (e == cudaSuccess) e = launch_solution(st->S, X, st->stream);
   if (e != cudaSuccess) return cuda_fail(e, "rg_solution: launch");
   if (rank_out) return rg_rank(st, rank_out);
   return RG_OK;
@@ -319,7 +361,8 @@ rg_status rg_adjoint(rg_state* st, const double* A, const double* y, int64_t n, 
   J.rho = p; p += std::max<int64_t>(n, 1);
   J.part = p;
   J.nrc = nrc;
-  e = launch_solution(S, J.X, st->stream);  // w and the Cholesky factor of P
+  e = launch_flush(flush_view(st), st->grid, st->stream);
+  if (e == cudaSuccess) e = launch_solution(S, J.X, st->stream);  // w and the Cholesky factor of P
   if (e == cudaSuccess) e = launch_adjoint(S, J, st->grid, st->stream);
   if (e == cudaSuccess && X) e = cudaMemcpyAsync(X, J.X, m * sizeof(double), cudaMemcpyDeviceToDevice, st->stream);
   const cudaError_t e2 = cudaFreeAsync(wk, st->stream);
@@ -335,7 +378,8 @@ rg_status rg_solution_host(rg_state* st, double* X, int64_t* rank_out) {
     cudaError_t e = cudaMalloc(&st->xbuf, (size_t)st->S.m * 8);
     if (e != cudaSuccess) return cuda_fail(e, "rg_solution_host: allocation");
   }
-  cudaError_t e = launch_solution(st->S, st->xbuf, st->stream);
+  cudaError_t e = launch_flush(flush_view(st), st->grid, st->stream);
+  if (e == cudaSuccess) e = launch_solution(st->S, st->xbuf, st->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(X, st->xbuf, (size_t)st->S.m * 8, cudaMemcpyDeviceToHost, st->stream);
   if (e != cudaSuccess) return cuda_fail(e, "rg_solution_host");
@@ -389,7 +433,8 @@ rg_status rg_export(rg_state* st, double* C, double* Ct, double* Pinv, double* w
   if (r > capacity) return fail(RG_EINVAL, "rg_export: rank %lld exceeds capacity %lld",
                                 (long long)r, (long long)capacity);
   cudaError_t e = cudaSuccess;
-  e = launch_export_prep(st->S, st->grid, st->stream);  // forms w and P^-1 from P
+  e = launch_flush(flush_view(st), st->grid, st->stream);
+  if (e == cudaSuccess) e = launch_export_prep(st->S, st->grid, st->stream);  // forms w and P^-1 from P
   if (e == cudaSuccess) e = launch_export(st->S, C, Ct, Pinv, w, (long long*)basis_rows, st->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
   if (e != cudaSuccess) return cuda_fail(e, "rg_export");

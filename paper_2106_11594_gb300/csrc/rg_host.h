@@ -19,6 +19,7 @@ cudaError_t launch_stream(const StreamDev& S, const double* Gamma, const double*
                           uint8_t* indep, int grid, cudaStream_t stream);
 cudaError_t stream_grid_size(int mixed, int* grid);
 cudaError_t launch_export_prep(const StreamDev& S, int grid, cudaStream_t stream);
+cudaError_t launch_flush(const StreamDev& S, int grid, cudaStream_t stream);
 cudaError_t launch_solution(const StreamDev& S, double* X, cudaStream_t stream);
 cudaError_t launch_export(const StreamDev& S, double* C, double* Ct, double* Pinv, double* w,
                           long long* basis, cudaStream_t stream);

@@ -35,6 +35,7 @@ enum : int {
   CTRL_RNEW = 8,       // block plan: rank after the block
   CTRL_NIND = 9,       // block plan: independent rows found in the block
   CTRL_PEND = 10,      // 1: u holds a correction not yet folded into w
+  CTRL_PEND_ROWS = 11, // rows of the previous call whose P/u update was deferred (in Gpend)
   CTRL_SUB_COUNT = 32, // barrier counter of the sequential section's column owners (words
                        // 32-33, a cache line apart from the grid barrier's counter)
   CTRL_N = 64
@@ -85,6 +86,14 @@ struct StreamDev {
   double* Sp;     // 2 x sp_stride: per-worker partial sums of the sequential section
   size_t sp_stride;  // >= 32 x (number of workers)
   void* tcx;      // tensor-core context of the CTA (struct TcCtx in shared memory) or null
+  // Deferred P/u update of small calls: a call of at most SMALL_B rows that ends with all
+  // rows dependent leaves its gammas (G) and a-priori errors (Dall) in place and records
+  // their count in CTRL_PEND_ROWS; the next call (whose G/Dall are the host's other pair
+  // of buffers, and whose Gpend/Dpend point here) folds them into P and u on CTAs that the
+  // rejection phase leaves idle, and rg_solution/rg_export fold them first.
+  double* Gpend;  // gammas of the pending rows (SMALL_B x r_max) or null (no deferral)
+  double* Dpend;  // their a-priori errors
+  int defer;      // 1: this call may defer (its G/Dall are a pending-capable pair)
   double* Kap;    // SLOW_MAX x SLOW_MAX: kappa of the section's later rows per append
   double* Rs;     // shared memory for the section's rejections (one-CTA team) or null
   long long rs_cap;  // doubles available at Rs

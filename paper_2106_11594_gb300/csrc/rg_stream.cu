@@ -48,8 +48,18 @@ __global__ void __launch_bounds__(NT, 1) stream_kernel(StreamDev S, CallArgs A) 
   process_rows<GridTeam, MIXED>(GridTeam{S.ctrl}, S, A);
 }
 
+// Folds the P/u update deferred by the last small call (if any) into P and u: every CTA
+// takes entries; the next kernel on the stream (form_w_kernel, export_prep_kernel) clears
+// the pending count.
+template <bool MIXED>
+__global__ void __launch_bounds__(NT, 1) flush_pending_kernel(StreamDev S) {
+  const int np = S.ctrl[CTRL_PEND_ROWS];
+  if (np > 0 && S.Gpend) acc_rows<GridTeam, MIXED>(GridTeam{S.ctrl}, S, S.Gpend, S.Dpend, 0, np, S.ctrl[CTRL_R], 0);
+}
+
 // w = w_b + P^-1 u (one CTA), then X = Ct^T w (general) or Q^T w (orthonormal).
 __global__ void __launch_bounds__(NT, 1) form_w_kernel(StreamDev S) {
+  if (threadIdx.x == 0) S.ctrl[CTRL_PEND_ROWS] = 0;
   form_w(S, S.ctrl[CTRL_R]);
 }
 __global__ void solution_kernel(StreamDev S, double* X) {
@@ -67,6 +77,7 @@ __global__ void solution_kernel(StreamDev S, double* X) {
 __global__ void __launch_bounds__(NT, 1) export_prep_kernel(StreamDev S) {
   grid_barrier_init(S.ctrl);
   const int r = ld_acquire_i32(S.ctrl + CTRL_R);
+  if (blockIdx.x == 0 && threadIdx.x == 0) S.ctrl[CTRL_PEND_ROWS] = 0;
   if (blockIdx.x == 0) form_w(S, r);
   if (!grid_barrier(S.ctrl)) return;
   form_pinv(GridTeam{S.ctrl}, S, r);
@@ -118,6 +129,13 @@ cudaError_t stream_grid_size(int mixed, int* grid) {
   if (e != cudaSuccess) return e;
   *grid = std::min(nsm, 1024) * (per >= 1 ? 1 : 0);  // the section scan holds <= 1024 workers
   return cudaSuccess;
+}
+
+cudaError_t launch_flush(const StreamDev& S, int grid, cudaStream_t stream) {
+  if (!S.Gpend) return cudaSuccess;
+  if (S.mixed) flush_pending_kernel<true><<<grid, NT, 0, stream>>>(S);
+  else flush_pending_kernel<false><<<grid, NT, 0, stream>>>(S);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_export_prep(const StreamDev& S, int grid, cudaStream_t stream) {
