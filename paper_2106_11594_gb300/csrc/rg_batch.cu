@@ -158,6 +158,9 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, co
       tcx.Blo = base + 3 * TC_TILE;
       tcx.bar = &tc_bar;
       tcx.phase = 0;
+      tcx.cache_cap = (TC_SMEM_MIXED - 1024) / 4 - 2 * TC_TILE;
+      tcx.cq = nullptr;
+      tcx.cr = -1;
     }
     tc_fence_before();
     __syncthreads();
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, co
   StreamDev S{};
   S.tcx = MIXED ? (void*)&tcx : nullptr;
   S.Rs = reinterpret_cast<double*>(dyn_base);
-  S.rs_cap = (TC_SMEM - 1024) / 8;
+  S.rs_cap = ((MIXED ? TC_SMEM_MIXED : TC_SMEM) - 1024) / 8;
   S.mixed = MIXED;
   S.test_mode = D.test_mode;
   S.tol = D.tol;
@@ -441,15 +444,16 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
   D.kb_max = std::min(kb, 256);
   int nsm = 0, per = 0;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, bt->device);
+  const int dyn = D.mixed ? TC_SMEM_MIXED : TC_SMEM;
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(D.mixed ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
   if (e == cudaSuccess)  // up to two CTAs of ~105 KiB each per SM
     e = cudaFuncSetAttribute(D.mixed ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per, D.mixed ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>, NT, TC_SMEM);
+        &per, D.mixed ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>, NT, dyn);
   if (e != cudaSuccess || per <= 0) {
     delete bt;
     return e != cudaSuccess ? cuda_fail(e, "rg_batch_init: occupancy") : fail(RG_ECUDA, "rg_batch_init: no occupancy");
@@ -532,7 +536,7 @@ rg_status rg_batch_add_rows(rg_batch* bt, const double* Gamma_packed, const int6
     // kernel writes every applied row and the rest are left as the caller initialised them
   }
   if (D.mixed)
-    batch_kernel<true><<<bt->grid, NT, TC_SMEM, bt->stream>>>(D, Gamma_packed, row_offsets, elem_offsets,
+    batch_kernel<true><<<bt->grid, NT, TC_SMEM_MIXED, bt->stream>>>(D, Gamma_packed, row_offsets, elem_offsets,
                                                         y_packed, indep_out);
   else
     batch_kernel<false><<<bt->grid, NT, TC_SMEM, bt->stream>>>(D, Gamma_packed, row_offsets, elem_offsets,

@@ -1265,6 +1265,8 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       phase_reject<Team, false, 1>(T, S, gam, q0, bend, r, S.C, S.R);
       if (!T.sync()) return false;
       if (!scan_team<Team, MIXED>(T, S, A, j0, q0, bend, r)) return false;
+      // the scan may have used the dynamic shared memory that caches the tensor-core B tiles
+      if (S.tcx && threadIdx.x == 0) reinterpret_cast<TcCtx*>(S.tcx)->cq = nullptr;
       if (!T.sync()) return false;
       if (threadIdx.x == 0) {
         sh[5] = __ldcg(S.ctrl + CTRL_APPLIED);  // published before the barrier above

@@ -33,6 +33,10 @@ constexpr int TC_N2 = 64;      // columns of m per second-product slice (MMA N)
 constexpr int TC_RMAX = 128;   // ranks handled (first-product N = r rounded up to 16)
 constexpr int TC_TILE = TC_M * TC_K;            // floats per operand tile (16 KiB)
 constexpr int TC_SMEM = 4 * TC_TILE * 4 + 1024;  // Ahi, Alo, Bhi, Blo + alignment slack
+// mixed-mode batch kernels (one CTA per SM) take more: Ahi, Alo, then either Bhi, Blo or a
+// cache of every B tile of the instance's current basis (both products), kept while the
+// basis does not change
+constexpr int TC_SMEM_MIXED = 180 * 1024;
 constexpr int TC_TMEM_COLS = 256;               // D1: columns [0, 128); D2: [128, 192)
 
 // Per-CTA tensor-core context (shared memory, written once by the kernel prologue except
@@ -40,11 +44,14 @@ constexpr int TC_TMEM_COLS = 256;               // D1: columns [0, 128); D2: [12
 struct TcCtx {
   float* Ahi;
   float* Alo;
-  float* Bhi;
+  float* Bhi;  // per-slice B tiles (uncached mode); the cache starts here too
   float* Blo;
   unsigned long long* bar;  // mbarrier: one arrival per commit
   uint32_t tmem;            // tensor-memory base (lane 0, column 0)
   uint32_t phase;           // parity of the next completion of `bar`
+  int cache_cap;            // floats available for the B-tile cache at Bhi (0: none)
+  const float* cq;          // basis whose tiles are cached (with rank cr), or null
+  int cr;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -139,9 +146,10 @@ __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
 }
 
 // One 32-wide K slice of D (+)= A B^T as 3xTF32 (four K steps of 8), issued by one thread.
-__device__ __forceinline__ void tc_slice_mma(const TcCtx& X, uint32_t d, int N, bool first) {
+__device__ __forceinline__ void tc_slice_mma_at(const float* Ahi, const float* Alo, const float* Bhi,
+                                                const float* Blo, uint32_t d, int N, bool first) {
   const uint32_t id = tc_idesc(TC_M, N);
-  const uint32_t ah = smem_u32(X.Ahi), al = smem_u32(X.Alo), bh = smem_u32(X.Bhi), bl = smem_u32(X.Blo);
+  const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const uint32_t o = (uint32_t)s * 256u;  // 8 TF32 = two core matrices along K
@@ -149,6 +157,9 @@ __device__ __forceinline__ void tc_slice_mma(const TcCtx& X, uint32_t d, int N, 
     tc_mma(d, tc_desc(ah + o), tc_desc(bl + o), id, 1u);
     tc_mma(d, tc_desc(al + o), tc_desc(bh + o), id, 1u);
   }
+}
+__device__ __forceinline__ void tc_slice_mma(const TcCtx& X, uint32_t d, int N, bool first) {
+  tc_slice_mma_at(X.Ahi, X.Alo, X.Bhi, X.Blo, d, N, first);
 }
 
 // A = rows [0, 128) x columns [k0, k0 + 32) of an FP64 row-major matrix (valid rows <
@@ -183,8 +194,8 @@ __device__ __forceinline__ void tc_store_a(const TcCtx& X, const double (&v)[16]
 
 // Stages B = rows [0, nrow) (multiple of 8) x columns [k0, k0 + 32) of the FP32 basis Qf
 // (rows >= r and columns >= m zero).
-__device__ __forceinline__ void tc_stage_q(const TcCtx& X, const float* __restrict__ Qf, int ld, int m,
-                                           int r, int nrow, int k0) {
+__device__ __forceinline__ void tc_stage_q_to(float* Bhi, float* Blo, const float* __restrict__ Qf, int ld,
+                                              int m, int r, int nrow, int k0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rl = lane >> 2, kl = lane & 3;
   // warp w takes column group kg = w of the row groups rg < nrow / 8 (at most 16); all
@@ -203,16 +214,20 @@ __device__ __forceinline__ void tc_stage_q(const TcCtx& X, const float* __restri
     if (rg < ngr) {
       float h, l;
       tf32_split(x[rg], h, l);
-      X.Bhi[o0 + rg * 256] = h;
-      X.Blo[o0 + rg * 256] = l;
+      Bhi[o0 + rg * 256] = h;
+      Blo[o0 + rg * 256] = l;
     }
   }
+}
+__device__ __forceinline__ void tc_stage_q(const TcCtx& X, const float* __restrict__ Qf, int ld, int m,
+                                           int r, int nrow, int k0) {
+  tc_stage_q_to(X.Bhi, X.Blo, Qf, ld, m, r, nrow, k0);
 }
 
 // Stages B = Q^T slice for the second product: row n < 64 is column c0 + n of Q, K index
 // k is basis row k1 + k (zero beyond r or m). Threads [t_lo, t_lo + 128) take part.
-__device__ __forceinline__ void tc_stage_qt(const TcCtx& X, const float* __restrict__ Qf, int ld, int m,
-                                            int r, int c0, int k1, int t_lo) {
+__device__ __forceinline__ void tc_stage_qt_to(float* Bhi, float* Blo, const float* __restrict__ Qf, int ld,
+                                               int m, int r, int c0, int k1, int t_lo) {
   const int t = threadIdx.x - t_lo;
   const int lane = t & 31, warp = t >> 5;  // 4 warps
   const int rl = lane >> 2, kl = lane & 3;
@@ -231,9 +246,13 @@ __device__ __forceinline__ void tc_stage_qt(const TcCtx& X, const float* __restr
     float h, l;
     tf32_split(x[q], h, l);
     const int o = rg * 256 + kg * 32 + rl * 4 + kl;
-    X.Bhi[o] = h;
-    X.Blo[o] = l;
+    Bhi[o] = h;
+    Blo[o] = l;
   }
+}
+__device__ __forceinline__ void tc_stage_qt(const TcCtx& X, const float* __restrict__ Qf, int ld, int m,
+                                            int r, int c0, int k1, int t_lo) {
+  tc_stage_qt_to(X.Bhi, X.Blo, Qf, ld, m, r, c0, k1, t_lo);
 }
 
 // A wait gave up: wait once more (bounded) for the MMAs in flight, so that the caller can
@@ -266,6 +285,27 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
   const uint32_t d1 = X.tmem, d2 = X.tmem + 128u;
   const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
   if (threadIdx.x == 0) q0_s = b;
+  // B-tile cache: tile (hi, lo) of first-product slice ks at cache + ks * 2 * n1 * 32,
+  // second-product tile (ns, k2) after them at + (ns * nk2 + k2) * 2 * 64 * 32
+  const int b1 = n1 * TC_K, b2 = TC_N2 * TC_K;  // floats per hi (or lo) tile
+  const bool cached = (long long)nks * 2 * b1 + (long long)nns * nk2 * 2 * b2 <= X.cache_cap;
+  float* const cache1 = X.Bhi;
+  float* const cache2 = X.Bhi + (size_t)nks * 2 * b1;
+  if (cached && !(X.cq == S.Qf && X.cr == r)) {
+    for (int ks = 0; ks < nks; ++ks)
+      tc_stage_q_to(cache1 + (size_t)ks * 2 * b1, cache1 + (size_t)ks * 2 * b1 + b1, S.Qf, ld, m, r, n1, ks * TC_K);
+    const int h = threadIdx.x >= 128 ? 1 : 0;  // the two halves take alternate tiles
+    for (int tix = h; tix < nns * nk2; tix += 2) {
+      const int ns = tix / nk2, k2 = tix - ns * nk2;
+      float* t = cache2 + (size_t)tix * 2 * b2;
+      tc_stage_qt_to(t, t + b2, S.Qf, ld, m, r, ns * TC_N2, k2 * TC_K, 128 * h);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Xp->cq = S.Qf;
+      Xp->cr = r;
+    }
+  }
   for (int row0 = 0; row0 < b; row0 += TC_M) {
     const int nrows = min(TC_M, b - row0);
     const double* src = gam + (size_t)row0 * m;
@@ -275,13 +315,18 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
     tc_load_a(av, src, m, nrows, 0);
     for (int ks = 0; ks < nks; ++ks) {
       tc_store_a(X, av);
-      tc_stage_q(X, S.Qf, ld, m, r, n1, ks * TC_K);
+      if (!cached) tc_stage_q(X, S.Qf, ld, m, r, n1, ks * TC_K);
       fence_async_smem();
       tc_fence_before();
       __syncthreads();
       if (threadIdx.x == 0) {
         tc_fence_after();
-        tc_slice_mma(X, d1, n1, ks == 0);
+        if (cached) {
+          const float* t = cache1 + (size_t)ks * 2 * b1;
+          tc_slice_mma_at(X.Ahi, X.Alo, t, t + b1, d1, n1, ks == 0);
+        } else {
+          tc_slice_mma(X, d1, n1, ks == 0);
+        }
         tc_commit(X.bar);
       }
       if (ks + 1 < nks) tc_load_a(av, src, m, nrows, (ks + 1) * TC_K);
@@ -319,7 +364,7 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
               X.Alo[o] = l;
             }
           }
-        } else {
+        } else if (!cached) {
           tc_stage_qt(X, S.Qf, ld, m, r, c0, k2 * TC_K, 128);
         }
         fence_async_smem();
@@ -327,7 +372,12 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
         __syncthreads();
         if (threadIdx.x == 0) {
           tc_fence_after();
-          tc_slice_mma(X, d2, TC_N2, k2 == 0);
+          if (cached) {
+            const float* t = cache2 + (size_t)(ns * nk2 + k2) * 2 * b2;
+            tc_slice_mma_at(X.Ahi, X.Alo, t, t + b2, d2, TC_N2, k2 == 0);
+          } else {
+            tc_slice_mma(X, d2, TC_N2, k2 == 0);
+          }
           tc_commit(X.bar);
         }
         if (!tc_wait(X.bar, ph)) return tc_timeout(S, Xp, ph);

@@ -219,3 +219,33 @@ def test_invalid_arguments():
     st = rg.RankGreville(4)
     with pytest.raises(rg.RGError):
         st.solution(None)
+
+
+@pytest.mark.parametrize("mode,tol", [(rg.RG_FP64, 1e-10), (rg.RG_MIXED, 1e-4)])
+def test_solutions_and_exports_between_calls_of_mixed_sizes(mode, tol):
+    """Calls of at most 64 rows defer their update of P and u to the next call; a
+    solution, an export or a larger call in between must see every row so far. X after
+    every call matches the oracle on the rows fed up to then."""
+    torch, dev = torch_cuda()
+    s = inputs.large_stream(900, 96, 12)
+    At = torch.from_numpy(s.A).to(dev)
+    Yt = torch.from_numpy(s.Y).to(dev)
+    st = rg.RankGreville(96, 1e-10, mode)
+    X = torch.empty(96, dtype=torch.float64, device=dev)
+    sizes = [7, 32, 64, 65, 1, 200, 32, 32, 3, 64, 400]
+    j0 = 0
+    for c, k in enumerate(sizes):
+        k = min(k, s.n - j0)
+        st.add_rows(At[j0:j0 + k], Yt[j0:j0 + k])
+        j0 += k
+        if c % 3 == 2:
+            cap = 96
+            C = torch.zeros(cap * 96, dtype=torch.float64, device=dev)
+            w = torch.zeros(cap, dtype=torch.float64, device=dev)
+            st.export(C, None, None, w, None, capacity=cap)
+        if c % 2 == 1 or j0 == s.n:
+            st.solution(X)
+            o = fp64.solve(s.A[:j0], s.Y[:j0], tol=1e-10)
+            assert checks.rel_err(X.cpu().numpy(), o.X) <= tol, (c, j0)
+    assert j0 == s.n
+    st.close()
