@@ -124,11 +124,12 @@ __host__ __device__ inline size_t scratch_layout(int kb, int ldm, int rmm, int n
   return off;
 }
 
-// Both modes take TC_SMEM bytes of dynamic shared memory: it holds the rejections of a
-// sequential section when they fit (m <= 256) and, in mixed mode, the operand tiles of the
-// tensor-core projection (never in use at the same time). Mixed mode also sets up the
-// CTA's tensor-core context: one mbarrier and TC_TMEM_COLS columns of tensor memory (at
-// most two CTAs per SM, so the 512 columns of an SM always suffice). FP64 mode runs two
+// Dynamic shared memory (TC_SMEM bytes in FP64 mode, TC_SMEM_MIXED in mixed mode) holds
+// the rejections of a sequential section when they fit and, in mixed mode, the operand
+// tiles and the B-tile cache of the tensor-core projection (never in use at the same
+// time). Mixed mode also sets up the
+// CTA's tensor-core context: one mbarrier and TC_TMEM_COLS columns of tensor memory (one
+// CTA per SM in mixed mode, so the 512 columns of an SM always suffice). FP64 mode runs two
 // CTAs per SM; mixed mode one, with the register budget that its staging needs.
 template <bool MIXED>
 __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, const double* __restrict__ Gp,
@@ -458,7 +459,7 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
     delete bt;
     return e != cudaSuccess ? cuda_fail(e, "rg_batch_init: occupancy") : fail(RG_ECUDA, "rg_batch_init: no occupancy");
   }
-  per = std::min(per, 2);  // tensor memory: TC_TMEM_COLS per CTA, 512 columns per SM
+  per = std::min(per, D.mixed ? 512 / TC_TMEM_COLS : 2);  // tensor memory: 512 columns per SM
   bt->grid = std::min<long long>((long long)nsm * per, B);
   // host-side layout
   std::vector<long long> soff(B), xoff(B + 1, 0);

@@ -37,7 +37,8 @@ constexpr int TC_SMEM = 4 * TC_TILE * 4 + 1024;  // Ahi, Alo, Bhi, Blo + alignme
 // cache of every B tile of the instance's current basis (both products), kept while the
 // basis does not change
 constexpr int TC_SMEM_MIXED = 180 * 1024;
-constexpr int TC_TMEM_COLS = 256;               // D1: columns [0, 128); D2: [128, 192)
+constexpr int TC_TMEM_COLS = 512;  // D1: columns [0, 128); D2 slices: 64 columns each from 128
+constexpr int TC_NG2 = 6;          // second-product column slices issued together (6 x 64 = 384)
 
 // Per-CTA tensor-core context (shared memory, written once by the kernel prologue except
 // `phase`, which thread 0 stores back at the end of every projection).
@@ -348,6 +349,64 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
     }
     // ---- second product per 64-column slice: GQ, then R = Gamma - GQ and the norms
     float s_acc = 0.f, t_acc = 0.f;
+    auto epilogue = [&](int ns, uint32_t dcol) {
+      // warp w reads lanes of its quarter, columns [32 half, 32 half + 32) of the slice
+      const int c0 = ns * TC_N2;
+      float gq[32];
+      tmem_ld32(X.tmem + lane_base + dcol + (uint32_t)(half * 32), gq);
+      if (row < nrows) {
+        const double* xr = src + (size_t)row * m;
+        const int cb = c0 + half * 32;
+#pragma unroll
+        for (int h2 = 0; h2 < 32; h2 += 16) {
+          double xv[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) xv[q] = (cb + h2 + q < m) ? __ldg(xr + cb + h2 + q) : 0.0;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const float xf = d2f_rz(xv[q]);
+            const float rv = (cb + h2 + q < m) ? xf - gq[h2 + q] : 0.f;
+            s_acc = fmaf(rv, rv, s_acc);
+            t_acc = fmaf(xf, xf, t_acc);
+          }
+        }
+      }
+    };
+    if (cached && nk2 == 1) {
+      // A = G staged once; up to TC_NG2 column slices issued back to back into their own
+      // accumulators (independent MMA chains), one commit and one wait per group
+      if (half == 0) {
+        float g[32];
+        tmem_ld32(d1 + lane_base, g);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          float h, l;
+          tf32_split(q < r ? g[q] : 0.f, h, l);
+          const int o = tc_off(row, q);
+          X.Ahi[o] = h;
+          X.Alo[o] = l;
+        }
+      }
+      for (int g0 = 0; g0 < nns; g0 += TC_NG2) {
+        const int ng = min(TC_NG2, nns - g0);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          tc_fence_after();
+          for (int q = 0; q < ng; ++q) {
+            const float* t = cache2 + (size_t)(g0 + q) * 2 * b2;
+            tc_slice_mma_at(X.Ahi, X.Alo, t, t + b2, d2 + (uint32_t)(q * TC_N2), TC_N2, true);
+          }
+          tc_commit(X.bar);
+        }
+        if (!tc_wait(X.bar, ph)) return tc_timeout(S, Xp, ph);
+        for (int q = 0; q < ng; ++q) epilogue(g0 + q, 128u + (uint32_t)(q * TC_N2));
+        tc_fence_before();
+        __syncthreads();  // the accumulators are free again
+        tc_fence_after();
+      }
+    } else
     for (int ns = 0; ns < nns; ++ns) {
       const int c0 = ns * TC_N2;
       for (int k2 = 0; k2 < nk2; ++k2) {
@@ -382,26 +441,7 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
         }
         if (!tc_wait(X.bar, ph)) return tc_timeout(S, Xp, ph);
       }
-      // epilogue: warp w reads lanes of its quarter, columns [32 half, 32 half + 32)
-      float gq[32];
-      tmem_ld32(d2 + lane_base + (uint32_t)(half * 32), gq);
-      if (row < nrows) {
-        const double* xr = src + (size_t)row * m;
-        const int cb = c0 + half * 32;
-#pragma unroll
-        for (int h2 = 0; h2 < 32; h2 += 16) {
-          double xv[16];
-#pragma unroll
-          for (int q = 0; q < 16; ++q) xv[q] = (cb + h2 + q < m) ? __ldg(xr + cb + h2 + q) : 0.0;
-#pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const float xf = d2f_rz(xv[q]);
-            const float rv = (cb + h2 + q < m) ? xf - gq[h2 + q] : 0.f;
-            s_acc = fmaf(rv, rv, s_acc);
-            t_acc = fmaf(xf, xf, t_acc);
-          }
-        }
-      }
+      epilogue(ns, 128u);
       tc_fence_before();
       __syncthreads();  // D2 and the staging buffers are free again
       tc_fence_after();
