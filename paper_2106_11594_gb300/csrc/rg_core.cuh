@@ -439,10 +439,12 @@ __device__ void phase_gamma_f32_staged(const Team& T, const StreamDev& S, const 
 // solution in base coordinates). Warp items, one row each.
 template <class Team>
 __device__ void phase_dall(const Team& T, const StreamDev& S, const CallArgs& A, long long j0, int b,
-                           int r) {
+                           int r, int w_first = 0) {
+  // rows are dealt to the workers starting at w_first (the ones another phase leaves idle)
   const int lane = threadIdx.x & 31;
   const long long wstride = (long long)T.size() * NWARP;
-  for (long long j = rr_warp(T); j < b; j += wstride) {
+  const int wid = (T.id() - w_first + T.size()) % T.size();
+  for (long long j = (long long)wid * NWARP + (threadIdx.x >> 5); j < b; j += wstride) {
     const double* g = S.G + (size_t)j * S.r_max;
     const double yv = __ldg(A.y + j0 + j);
     double acc = 0.0;
@@ -1216,12 +1218,12 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       // 2: rejections and norms; a-priori errors against w_b
       if (big_rej) phase_reject<Team, MIXED, 8>(T, S, gam, 0, b, r, S.C, nullptr);
       else phase_reject<Team, MIXED, 1>(T, S, gam, 0, b, r, S.C, nullptr);
-      phase_dall(T, S, A, j0, b, r);
-      if (sh[4] > 0) {  // the previous call's deferred P/u update, on the idle CTAs
-        const long long nrej = (long long)((b + 4 * (big_rej ? 8 : 1) - 1) / (4 * (big_rej ? 8 : 1))) * S.nmc;
-        const int w_lo = (int)min(nrej, (long long)max(0, T.size() - 16));
-        acc_rows<Team, MIXED>(T, S, S.Gpend, S.Dpend, 0, sh[4], r, w_lo);
-      }
+      // CTAs beyond the rejection items take the a-priori errors and the previous call's
+      // deferred P/u update
+      const long long nrej = (long long)((b + 4 * (big_rej ? 8 : 1) - 1) / (4 * (big_rej ? 8 : 1))) * S.nmc;
+      const int w_lo = (int)min(nrej, (long long)max(0, T.size() - 16));
+      phase_dall(T, S, A, j0, b, r, w_lo);
+      if (sh[4] > 0) acc_rows<Team, MIXED>(T, S, S.Gpend, S.Dpend, 0, sh[4], r, w_lo);
       if (!T.sync()) return false;
       // 3: decide
       if (b <= SMALL_B) {
