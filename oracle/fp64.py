@@ -47,6 +47,10 @@ def lib():
                                         ctypes.c_int, f64p, i64p, i64p, u8p, f64p, f64p, f64p,
                                         i64p]
             L.rgo_solve_mut.restype = ctypes.c_int
+            L.rgo_solve_var.argtypes = [i64, i64, f64p, f64p, ctypes.c_double, ctypes.c_int, i64,
+                                        ctypes.c_int, ctypes.c_int, f64p, i64p, i64p, u8p, f64p,
+                                        f64p, f64p, i64p]
+            L.rgo_solve_var.restype = ctypes.c_int
             L.rgo_solve_batch.argtypes = [i64, i64p, i64p, i64p, f64p, f64p, ctypes.c_double,
                                           ctypes.c_int, ctypes.c_int, f64p, i64p, ctypes.c_void_p]
             L.rgo_solve_batch.restype = ctypes.c_int
@@ -72,9 +76,13 @@ class Result:
     status: int
 
 
+GENERAL, ORTHONORMAL = 0, 1
+
+
 def solve(A, Y, tol: float = 1e-10, test_mode: int = TEST_REL, r_max: int = 0,
-          mutation: int = 0) -> Result:
-    """Run Algorithm 1 over all rows of A (n x m) with targets Y, from an empty state."""
+          mutation: int = 0, variant: int = GENERAL) -> Result:
+    """Run Algorithm 1 over all rows of A (n x m) with targets Y, from an empty state.
+    variant=ORTHONORMAL takes Section 2.2's orthonormal rank factorization (C = Ct = Q)."""
     A = np.ascontiguousarray(A, dtype=np.float64)
     Y = np.ascontiguousarray(Y, dtype=np.float64).reshape(-1)
     n, m = A.shape
@@ -88,9 +96,9 @@ def solve(A, Y, tol: float = 1e-10, test_mode: int = TEST_REL, r_max: int = 0,
     C = np.zeros(rm * m)
     Pinv = np.zeros(rm * rm)
     done = np.zeros(1, dtype=np.int64)
-    st = lib().rgo_solve_mut(n, m, _ptr(A), _ptr(Y), float(tol), int(test_mode), int(r_max),
-                             int(mutation), _ptr(X), _ptr(rank), _ptr(basis), _ptr(indep),
-                             _ptr(Ct), _ptr(Pinv), _ptr(C), _ptr(done))
+    st = lib().rgo_solve_var(n, m, _ptr(A), _ptr(Y), float(tol), int(test_mode), int(r_max),
+                             int(variant), int(mutation), _ptr(X), _ptr(rank), _ptr(basis),
+                             _ptr(indep), _ptr(Ct), _ptr(Pinv), _ptr(C), _ptr(done))
     if st not in (0, 4):
         raise RuntimeError(f"rgo_solve failed with status {st}")
     r = int(rank[0])

@@ -21,6 +21,15 @@
  *       P^-1 = P^-1 - zeta zeta^T / (1 + gamma^T zeta)  (Eq. label_eq_Pnplusoneinv_lindep_update)
  *   X = X + K (y - Gamma^T X)                       (Eq. label_eq_recursive_least_squares)
  *
+ * Orthonormal variant (Section 2.2, Eqs. label_eq_Cnplusone_indep_update_orthog,
+ * label_eq_Cnplusonetilde_indep_update_orthog, label_eq_Pnplusoneinv_indep_update_orthog
+ * with alpha = 1 / ||Gamma_r||): an independent row instead stores
+ *       C    = [C ; alpha Gamma_r^T],   Ct = [Ct ; Gamma_r^T / (alpha ||Gamma_r||^2)]
+ *       P^-1 = [[P^-1, -alpha zeta], [-alpha zeta^T, alpha^2 (1 + gamma^T zeta)]],
+ *              zeta = P^-1 gamma
+ * (so the rows of C are orthonormal and Ct = C); K, the dependent case and the X update
+ * are unchanged, since Theorems 4 and 5 hold for any rank factorization.
+ *
  * Readings of the paper taken here (each listed in the design notes):
  *  - Threshold (Eq. label_eq_eps). Two modes. REL (default): independent iff
  *    ||Gamma_r|| > eps ||Gamma||. PAPER: dependent iff ||Gamma_r|| < eps or
@@ -54,6 +63,7 @@ typedef struct {
   double tol;
   int test_mode;
   int mutation;
+  int variant;  /* 0: general (Algorithm 1), 1: orthonormal (Section 2.2) */
   double *C;    /* r_max x m, row i = i-th basis row (a selected input row)      */
   double *Ct;   /* r_max x m, row i = i-th dual basis row                          */
   double *Pinv; /* r_max x r_max, leading r x r block is P^-1 = (B^T B)^-1         */
@@ -129,7 +139,34 @@ static int rgo_update(rgo_state *st, const double *G, double y) {
     t += G[c] * G[c];
   }
   int indep = rgo_is_independent(st, s, t);
-  if (indep) {
+  if (indep && st->variant == 1) {
+    if (r >= st->r_max) return -4;
+    const double alpha = 1.0 / sqrt(s);
+    /* zeta <- P^-1 gamma (for the bordered P^-1) */
+    for (int64_t i = 0; i < r; ++i) {
+      double acc = 0.0;
+      for (int64_t j = 0; j < r; ++j) acc += PI(i, j) * st->gamma[j];
+      st->zeta[i] = acc;
+    }
+    double gz = 0.0;
+    for (int64_t i = 0; i < r; ++i) gz += st->gamma[i] * st->zeta[i];
+    /* K <- Gamma_r / ||Gamma_r||^2 */
+    for (int64_t c = 0; c < m; ++c) st->K[c] = st->Gr[c] / s;
+    /* C <- [C ; alpha Gamma_r^T], Ct <- [Ct ; Gamma_r^T / (alpha ||Gamma_r||^2)] */
+    for (int64_t c = 0; c < m; ++c) {
+      CM(r, c) = alpha * st->Gr[c];
+      CT(r, c) = st->Gr[c] / (alpha * s);
+    }
+    /* P^-1 <- [[P^-1, -alpha zeta], [-alpha zeta^T, alpha^2 (1 + gamma^T zeta)]] */
+    const double sg = (mut == 9 ? 1.0 : -1.0);
+    for (int64_t i = 0; i < r; ++i) {
+      PI(i, r) = sg * alpha * st->zeta[i];
+      PI(r, i) = sg * alpha * st->zeta[i];
+    }
+    PI(r, r) = (mut == 8 ? 1.0 + gz : alpha * alpha * (1.0 + gz));
+    st->basis_rows[r] = st->rows_seen;
+    st->r = r + 1;
+  } else if (indep) {
     if (r >= st->r_max) return -4;
     /* K <- Gamma_r / ||Gamma_r||^2 */
     for (int64_t c = 0; c < m; ++c) st->K[c] = st->Gr[c] / s;
@@ -188,10 +225,10 @@ static int rgo_update(rgo_state *st, const double *G, double y) {
  * Returns 0, 1 (bad arguments), 2 (out of memory) or 4 (rank would exceed r_max; rows
  * before the offending row are applied, rows_done says how many).
  */
-int rgo_solve_mut(int64_t n, int64_t m, const double *A, const double *Y, double tol,
-                  int test_mode, int64_t r_max, int mutation, double *X, int64_t *rank_out,
-                  int64_t *basis_rows, uint8_t *indep, double *Ct_out, double *Pinv_out,
-                  double *C_out, int64_t *rows_done) {
+int rgo_solve_var(int64_t n, int64_t m, const double *A, const double *Y, double tol,
+                  int test_mode, int64_t r_max, int variant, int mutation, double *X,
+                  int64_t *rank_out, int64_t *basis_rows, uint8_t *indep, double *Ct_out,
+                  double *Pinv_out, double *C_out, int64_t *rows_done) {
   if (n < 0 || m <= 0 || (n > 0 && (!A || !Y)) || tol != tol) return 1;
   if (r_max <= 0) r_max = m;
   if (r_max > m) r_max = m;
@@ -201,6 +238,7 @@ int rgo_solve_mut(int64_t n, int64_t m, const double *A, const double *Y, double
     return 2;
   }
   st.mutation = mutation;
+  st.variant = variant;
   int status = 0;
   int64_t i = 0;
   for (; i < n; ++i) {
@@ -223,6 +261,14 @@ int rgo_solve_mut(int64_t n, int64_t m, const double *A, const double *Y, double
   }
   rgo_release(&st);
   return status;
+}
+
+int rgo_solve_mut(int64_t n, int64_t m, const double *A, const double *Y, double tol,
+                  int test_mode, int64_t r_max, int mutation, double *X, int64_t *rank_out,
+                  int64_t *basis_rows, uint8_t *indep, double *Ct_out, double *Pinv_out,
+                  double *C_out, int64_t *rows_done) {
+  return rgo_solve_var(n, m, A, Y, tol, test_mode, r_max, 0, mutation, X, rank_out, basis_rows,
+                       indep, Ct_out, Pinv_out, C_out, rows_done);
 }
 
 int rgo_solve(int64_t n, int64_t m, const double *A, const double *Y, double tol,

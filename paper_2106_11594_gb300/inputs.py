@@ -23,6 +23,8 @@ from __future__ import annotations
 
 import dataclasses
 
+from typing import Optional
+
 import numpy as np
 
 BASE_SEED = 2106_11594
@@ -42,6 +44,7 @@ class Stream:
     Y: np.ndarray  # n, float64
     rank: int  # rank of the generator (the exact rank of the factor product)
     name: str = ""
+    growth: Optional[np.ndarray] = None  # n, uint8: 1 where the generator's prefix rank grows
 
     @property
     def n(self) -> int:
@@ -197,8 +200,16 @@ def ill_conditioned_stream(n: int = 32768, m: int = 2048, r: int = 256, phases: 
         A[i] = c @ A[src]
     x_true = rng.standard_normal(m)
     Y = A @ x_true + rng.standard_normal(n) * 1e-3
+    # The prefix rank grows on the first `step` rows of each phase that are not
+    # combinations (generically: those rows' new coordinates form a nonsingular block).
+    growth = np.zeros(n, dtype=np.uint8)
+    combo = np.zeros(n, dtype=bool)
+    combo[pos] = True
+    for p0 in range(0, n, per):
+        fresh = [i for i in range(p0, min(n, p0 + per)) if not combo[i]]
+        growth[fresh[:step]] = 1
     return Stream(A=np.ascontiguousarray(A), Y=Y, rank=r,
-                  name=f"ill-conditioned stream n={n} m={m} r={r}")
+                  name=f"ill-conditioned stream n={n} m={m} r={r}", growth=growth)
 
 
 # ---------------------------------------------------------------------------

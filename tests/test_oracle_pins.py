@@ -19,10 +19,10 @@ from paper_2106_11594_gb300 import inputs
 GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
 
 
-def pinv_by_unit_targets(A, tol):
+def pinv_by_unit_targets(A, tol, variant=fp64.GENERAL):
     """A^+ column by column: X(Y = e_j) = A^+ e_j (X is linear in Y, Section 1)."""
     n = A.shape[0]
-    return np.stack([fp64.solve(A, np.eye(n)[j], tol=tol).X for j in range(n)], axis=1)
+    return np.stack([fp64.solve(A, np.eye(n)[j], tol=tol, variant=variant).X for j in range(n)], axis=1)
 
 
 def prefix_rank_trajectory(Afr):
@@ -349,3 +349,91 @@ def test_planted_mistake_is_caught(mutation):
     res = fp64.solve(s.A, s.Y, tol=1e-10, mutation=mutation)
     caught.append(checks.rel_err(res.X, np.linalg.lstsq(s.A, s.Y, rcond=1e-10)[0]) > 1e-10)
     assert any(caught), MUTATIONS[mutation]
+
+
+# ---------------------------------------------------------------------------------------
+# Orthonormal variant (Section 2.2, alpha = 1 / ||Gamma_r||)
+# ---------------------------------------------------------------------------------------
+
+def _rank_deficient(n, m, r, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, r)) @ rng.standard_normal((r, m))
+    Y = rng.standard_normal(n)
+    return A, Y
+
+
+def test_orthonormal_variant_matches_svd_least_squares():
+    for (n, m, r, seed) in [(40, 12, 5, 1), (12, 30, 7, 2), (60, 20, 20, 3)]:
+        A, Y = _rank_deficient(n, m, r, seed)
+        o = fp64.solve(A, Y, tol=1e-10, variant=fp64.ORTHONORMAL)
+        assert o.rank == min(n, m, r)
+        Xs = np.linalg.lstsq(A, Y, rcond=None)[0]
+        assert checks.rel_err(o.X, Xs) < 1e-11
+
+
+def test_orthonormal_variant_basis_and_inverse():
+    A, Y = _rank_deficient(50, 16, 6, 4)
+    o = fp64.solve(A, Y, tol=1e-10, variant=fp64.ORTHONORMAL)
+    Q = o.C
+    assert np.abs(Q @ Q.T - np.eye(o.rank)).max() < 1e-13  # rows orthonormal
+    assert np.abs(o.Ct - Q).max() < 1e-13  # the dual basis is Q itself
+    B = A @ Q.T
+    assert np.abs(o.Pinv @ (B.T @ B) - np.eye(o.rank)).max() < 1e-10  # P^-1 = (B^T B)^-1
+    assert max(checks.penrose_residuals(A, checks.pinv_from_factors(A, o.Ct, o.Pinv))) < 1e-12
+
+
+def test_orthonormal_and_general_agree_and_follow_the_prefix_rank():
+    A, Y = _rank_deficient(24, 9, 4, 5)
+    A[5] = A[2] + A[3]
+    A[9] = 0.0
+    g = fp64.solve(A, Y, tol=1e-10)
+    o = fp64.solve(A, Y, tol=1e-10, variant=fp64.ORTHONORMAL)
+    np.testing.assert_array_equal(g.indep, o.indep)
+    prefix = [np.linalg.matrix_rank(A[:i + 1]) for i in range(A.shape[0])]
+    expect = np.diff([0] + prefix).astype(np.uint8)
+    np.testing.assert_array_equal(o.indep, expect)
+    assert checks.rel_err(o.X, g.X) < 1e-11
+
+
+def test_golden_orthonormal_variant_metrics():
+    """The orthonormal columns of Tables table_e_Pascal / table_res_Pascal,
+    table_e_USV / table_res_USV and table_res_Kahan: the orthonormal oracle lands within
+    the same factors as the general one (30 for Pascal and the USV medians, 3 for Kahan).
+    A printed residual within 100 machine epsilons of zero (P(4): 1.83e-15) is rounding
+    noise whose size depends on the operation order, so there only the upper bound holds."""
+    eps_m = GOLDEN["machine_epsilon"]["eps_M"]
+    g = GOLDEN["pascal"]
+    for n, e_ref, r_ref in zip(g["n"], g["e_orthonormal"], g["res_orthonormal"]):
+        A = inputs.pascal(n)
+        Linv = np.array([[(-1) ** (i - j) * comb(i, j) for j in range(n)] for i in range(n)], float)
+        Ap = pinv_by_unit_targets(A, 1e-30, fp64.ORTHONORMAL)
+        e = checks.stability_factor(Ap, Linv.T @ Linv, A)
+        res = checks.residual_error(Ap, A)
+        assert e_ref / 30 <= e <= e_ref * 30, (n, e, e_ref)
+        lo = r_ref / 30 if r_ref > 100 * eps_m else 0.0
+        assert lo <= res <= r_ref * 30, (n, res, r_ref)
+    g = GOLDEN["usv"]
+    for n, e_ref, r_ref in zip(g["n"], g["e_orthonormal"], g["res_orthonormal"]):
+        es, rs = [], []
+        for seed in range(5):
+            A, U, S, V = inputs.usv(n, seed)
+            Ap = pinv_by_unit_targets(A, g["eps"], fp64.ORTHONORMAL)
+            ref = V @ np.diag(1 / np.diag(S)) @ U.T
+            es.append(checks.stability_factor(Ap, ref, A))
+            rs.append(checks.residual_error(Ap, A))
+        assert e_ref / 30 <= np.median(es) <= e_ref * 30, (n, es, e_ref)
+        assert r_ref / 30 <= np.median(rs) <= r_ref * 30, (n, rs, r_ref)
+    g = GOLDEN["kahan"]
+    for c, ref in zip(g["c"], g["res_orthonormal"]):
+        A = inputs.kahan(g["n"], c)
+        res = checks.residual_error(pinv_by_unit_targets(A, 1e-30, fp64.ORTHONORMAL), A)
+        assert ref / 3 <= res <= ref * 3, (c, res, ref)
+
+
+@pytest.mark.parametrize("mutation", [8, 9])
+def test_orthonormal_planted_mistakes_fail_a_pin(mutation):
+    A, Y = _rank_deficient(40, 12, 5, 6)
+    o = fp64.solve(A, Y, tol=1e-10, variant=fp64.ORTHONORMAL, mutation=mutation)
+    Xs = np.linalg.lstsq(A, Y, rcond=None)[0]
+    assert checks.rel_err(o.X, Xs) > 1e-6 or np.abs(
+        o.Pinv @ ((A @ o.C.T).T @ (A @ o.C.T)) - np.eye(o.rank)).max() > 1e-6
