@@ -38,7 +38,7 @@ METRIC = ("row updates/sec (device-timed, batched & single) at stated rel. error
 WORKLOAD = f"single FP64 stream n={N_ROWS} m={M} r={R}, k={K_CALL} rows per rg_add_rows call"
 
 
-# DRAM bytes (read + write) of one 32-row stream_kernel<false> launch, from the ncu capture
+# DRAM bytes (read + write) of one 32-row stream_kernel<false, false> launch, from the ncu capture
 # summarised in profiles/stream_kernel_fp64_k32_n4096_full.md, and the hash of the kernel
 # sources it was taken on: once the sources change the figure no longer applies (null).
 TRAFFIC_BYTES_PER_LAUNCH = 1465856
@@ -274,7 +274,7 @@ def run_gpu(args):
                 "frac": achieved / peak, "traffic": measured_traffic(),
                 "peak_source": f"FP64 vector peak derived: 152 SMs x 4 flop/clk x {sm_mhz:.0f} MHz "
                                "(median SM clock sampled during the timed region)",
-                "kernel": "rg::stream_kernel<false> (one launch per 32-row call)",
+                "kernel": "rg::stream_kernel<false, false> (one launch per 32-row call)",
                 "avg_launch_ms": launch_ms}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": ws,

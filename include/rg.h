@@ -58,8 +58,13 @@ enum {
   RG_MIXED = 1,       /* projections in FP32; rank test, denominators, P^-1 and w in
                          FP64; candidate rows are re-decided in FP64 (see rg_init)   */
   RG_TEST_REL = 0,    /* independent iff ||Gamma_r|| > eps ||Gamma||                  */
-  RG_TEST_PAPER = 2   /* dependent iff ||Gamma_r|| < eps or ||Gamma_r|| < eps ||Gamma||
+  RG_TEST_PAPER = 2,  /* dependent iff ||Gamma_r|| < eps or ||Gamma_r|| < eps ||Gamma||
                          (Eq. label_eq_eps, both clauses)                            */
+  RG_ORTHONORMAL = 4  /* keep the orthonormal variant of Section 2.2 (alpha_{n+1} =
+                         1/||Gamma_r||: the basis rows are orthonormal and serve as their
+                         own dual basis) instead of Algorithm 1's raw rows and dual basis.
+                         RG_MIXED always uses it; with RG_FP64 it is opt-in (rg_init and
+                         rg_solve_noalloc; not rg_batch_init)                        */
 };
 
 /*
@@ -69,8 +74,8 @@ enum {
  *   tol        rank-test threshold eps of Eq. label_eq_eps. tol <= 0 selects the
  *              paper's default (m^2 r + m r + m) eps_M, r the rank before the row.
  *              Must not be NaN.
- *   flags      RG_FP64 or RG_MIXED, OR-ed with RG_TEST_REL or RG_TEST_PAPER.
- *              In RG_MIXED mode a row whose FP32 relative rejection
+ *   flags      RG_FP64 or RG_MIXED, OR-ed with RG_TEST_REL or RG_TEST_PAPER and
+ *              optionally RG_ORTHONORMAL. In RG_MIXED mode a row whose FP32 relative rejection
  *              ||Gamma_r|| / ||Gamma|| exceeds 1e-5 is recomputed and decided in FP64;
  *              rows below that floor are taken as dependent.
  *   r_max      capacity of the basis (maximum rank), 1..m; <= 0 means m.
@@ -97,8 +102,11 @@ rg_status rg_add_rows(rg_state* st, const double* Gamma, const double* y, int64_
 
 /*
  * rg_add_rows_host -- same as rg_add_rows for HOST buffers: the rows are copied to the
- * device inside the call (in chunks through library-owned staging memory) and the call
- * returns once the host buffers may be reused. indep_out is host memory (may be NULL).
+ * device inside the call (in chunks through two library-owned staging slots, on a copy
+ * stream of the library, so that a chunk's copy overlaps the previous update) and the call
+ * returns once the host buffers may be reused; the update itself stays asynchronous
+ * (device errors surface at the next synchronising call). indep_out is host memory (may be
+ * NULL); when given, the call also waits for the update.
  */
 rg_status rg_add_rows_host(rg_state* st, const double* Gamma, const double* y, int64_t k,
                            uint8_t* indep_out);
@@ -131,6 +139,17 @@ rg_status rg_adjoint(rg_state* st, const double* A, const double* y, int64_t n, 
 
 /* rg_solution_host -- rg_solution into HOST memory X (m doubles). Synchronising. */
 rg_status rg_solution_host(rg_state* st, double* X, int64_t* rank_out);
+
+/*
+ * rg_set_screen -- mixed mode only: floor tau_lo of the FP32 screen (default 1e-5). A row
+ * whose FP32 relative rejection ||Gamma_r|| / ||Gamma|| is at most max(tau_lo, tol / 2) is
+ * declared dependent without an FP64 decision; rows above it are re-decided in FP64 against
+ * tol. Lowering it catches rejections between tol and the default floor (ill-conditioned
+ * inputs, Section 4.2's stability discussion) at the price of more FP64 decisions; below
+ * the FP32 noise of the projections (~1e-7 relative) every row is decided in FP64.
+ * 0 < tau_lo < 1, else RG_EINVAL. Host-side only; applies from the next call.
+ */
+rg_status rg_set_screen(rg_state* st, double tau_lo);
 
 /* rg_rank -- current rank r into *rank_out (host). Synchronising. */
 rg_status rg_rank(rg_state* st, int64_t* rank_out);
@@ -216,6 +235,9 @@ rg_status rg_batch_adjoint(rg_batch* bt, const double* Gamma_packed, const int64
                            const int64_t* elem_offsets, const double* y_packed, int64_t total_rows,
                            const double* g_packed, const int64_t* x_offsets, double* gA_packed,
                            double* gy_packed);
+
+/* rg_batch_set_screen -- rg_set_screen for every instance of the batch. */
+rg_status rg_batch_set_screen(rg_batch* bt, double tau_lo);
 
 /* rg_batch_set_stream -- issue later batch calls on cuda_stream (synchronises the old
  * stream first). Lets a caller capture the batch calls into a CUDA graph. */

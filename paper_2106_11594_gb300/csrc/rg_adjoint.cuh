@@ -75,7 +75,7 @@ __device__ void adj_cols(const Team& T, const double* D, int ld, int m, int r, c
 template <class Team>
 __device__ bool adjoint_run(const Team& T, const StreamDev& S, const AdjArgs& J, int r) {
   const int m = S.m, ld = S.ld, rm = S.r_max;
-  const double* D = S.mixed ? S.C : S.Ct;
+  const double* D = S.ortho ? S.C : S.Ct;
   const double* Cb = S.C;
   const long long n = J.n;
   const int lane = threadIdx.x & 31;

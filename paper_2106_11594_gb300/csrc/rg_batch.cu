@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, co
   S.Rs = reinterpret_cast<double*>(dyn_base);
   S.rs_cap = ((MIXED ? TC_SMEM_MIXED : TC_SMEM) - 1024) / 8;
   S.mixed = MIXED;
+  S.ortho = MIXED;
   S.test_mode = D.test_mode;
   S.tol = D.tol;
   S.tau_lo = D.tau_lo;
@@ -327,6 +328,7 @@ __global__ void __launch_bounds__(NT, 2) batch_adjoint_kernel(BatchDev D, const 
     S.ld = (m + 3) / 4 * 4;
     S.r_max = D.r_max[b];
     S.mixed = D.mixed;
+    S.ortho = D.mixed;
     S.ctrl = D.ctrl + (size_t)b * CTRL_N;
     inst_layout(m, S.ld, S.r_max, D.mixed, D.state + D.soff[b], &S);
     const int r = D.ctrl[(size_t)b * CTRL_N + CTRL_R];
@@ -406,7 +408,9 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
   if (B <= 0 || B > (1 << 20)) return fail(RG_EINVAL, "rg_batch_init: B = %lld out of range", (long long)B);
   if (!m) return fail(RG_EINVAL, "rg_batch_init: m is NULL");
   if (std::isnan(tol)) return fail(RG_EINVAL, "rg_batch_init: tol is NaN");
-  if (flags & ~(RG_MIXED | RG_TEST_PAPER)) return fail(RG_EINVAL, "rg_batch_init: unknown flags %d", flags);
+  if (flags & ~(RG_MIXED | RG_TEST_PAPER | RG_ORTHONORMAL)) return fail(RG_EINVAL, "rg_batch_init: unknown flags %d", flags);
+  if ((flags & RG_ORTHONORMAL) && !(flags & RG_MIXED))
+    return fail(RG_EINVAL, "rg_batch_init: the FP64 orthonormal variant is available for single streams only");
   rg_batch* bt = new (std::nothrow) rg_batch();
   if (!bt) return fail(RG_ENOMEM, "rg_batch_init: host allocation failed");
   bt->m.resize(B);
@@ -607,6 +611,13 @@ rg_status rg_batch_set_stream(rg_batch* bt, void* cuda_stream) {
   cudaError_t e = cudaStreamSynchronize(bt->stream);
   if (e != cudaSuccess) return cuda_fail(e, "rg_batch_set_stream");
   bt->stream = (cudaStream_t)cuda_stream;
+  return RG_OK;
+}
+
+rg_status rg_batch_set_screen(rg_batch* bt, double tau_lo) {
+  if (!valid_batch(bt)) return fail(RG_EINVAL, "rg_batch_set_screen: invalid batch");
+  if (!(tau_lo > 0.0 && tau_lo < 1.0)) return fail(RG_EINVAL, "rg_batch_set_screen: tau_lo = %g outside (0, 1)", tau_lo);
+  bt->D.tau_lo = tau_lo;
   return RG_OK;
 }
 

@@ -1124,7 +1124,8 @@ __device__ void section_apply_pu(const Team& T, const StreamDev& S, int q0, int 
 // Appends of the sequential section to the basis, team-wide.
 // General variant: Ct_final[i] = base_i - sum_{q >= qmin(i)} Gind[q][i] K_q with
 // base_i = Ct[i] (i < r) or K_{i-r}, qmin(i) = max(0, i - r + 1); C[r + q] = Gamma_{jind[q]}.
-// Orthonormal variant: Q[r + q] = alpha_q Gamma_r (already scaled in Kv) and its FP32 copy.
+// Orthonormal variant: Q[r + q] = alpha_q Gamma_r (already scaled in Kv) and, with FP32
+// projections, its FP32 copy.
 template <class Team, bool ORTHO>
 __device__ void section_apply_basis(const Team& T, const StreamDev& S, const CallArgs& A, long long j0,
                                     int r, int nind) {
@@ -1137,7 +1138,7 @@ __device__ void section_apply_basis(const Team& T, const StreamDev& S, const Cal
       const int q = (int)(e / m), c = (int)(e - (long long)q * m);
       const double v = __ldcg(S.Kv + (size_t)q * ld + c);
       S.C[(size_t)(r + q) * ld + c] = v;
-      S.Qf[(size_t)(r + q) * ld + c] = (float)v;
+      if (S.Qf) S.Qf[(size_t)(r + q) * ld + c] = (float)v;
     }
     return;
   }
@@ -1170,7 +1171,7 @@ __device__ void section_apply_basis(const Team& T, const StreamDev& S, const Cal
 //  * otherwise: worker 0 decides; the dependent run before the first special row is
 //    accumulated; from that row the sequential FP64 section applies the rank changes.
 // =======================================================================================
-template <class Team, bool MIXED>
+template <class Team, bool F32, bool ORTHO = F32>
 __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& A) {
   __shared__ int sh[8];
   long long j0 = 0;
@@ -1192,7 +1193,7 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
     // mixed mode, one CTA per stream, large blocks: projection, rejection norms and the
     // FP32 screen on the tensor cores (q0 = first row the screen cannot clear)
     int q0 = -2;
-    if constexpr (MIXED && std::is_same<Team, CtaTeam>::value) {
+    if constexpr (F32 && std::is_same<Team, CtaTeam>::value) {
       if (S.tcx && b > SMALL_B && r >= 1 && r <= TC_RMAX) {
         double tcut = S.tau_lo;
         if (S.test_mode == 0 && S.tol > 0.0) tcut = fmax(tcut, 0.5 * S.tol);
@@ -1208,29 +1209,29 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       // larger items only while they still give every worker at least two
       const bool big_rej = (long long)(b / 32) * S.nmc >= 2LL * T.size();
       const int gr = min(8, (int)((POOL_DOUBLES * 2) / max(S.m, 1)));  // FP32 rows that fit
-      if (MIXED && gr >= 1 && (long long)(b / gr) >= 2LL * T.size())
+      if (F32 && gr >= 1 && (long long)(b / gr) >= 2LL * T.size())
         phase_gamma_f32_staged(T, S, gam, 0, b, r, gr);
-      else if (!MIXED && (long long)((b + 7) / 8) * r < 4LL * NWARP * T.size())
-        phase_gamma_cta(T, S, gam, 0, b, r, S.Ct);  // few warp items: split each over a CTA
+      else if (!F32 && (long long)((b + 7) / 8) * r < 4LL * NWARP * T.size())
+        phase_gamma_cta(T, S, gam, 0, b, r, ORTHO ? S.C : S.Ct);  // few warp items: split each over a CTA
       else
-        phase_gamma<Team, MIXED>(T, S, gam, 0, b, r, MIXED ? S.C : S.Ct);
+        phase_gamma<Team, F32>(T, S, gam, 0, b, r, ORTHO ? S.C : S.Ct);
       if (!T.sync()) return false;
       // 2: rejections and norms; a-priori errors against w_b
-      if (big_rej) phase_reject<Team, MIXED, 8>(T, S, gam, 0, b, r, S.C, nullptr);
-      else phase_reject<Team, MIXED, 1>(T, S, gam, 0, b, r, S.C, nullptr);
+      if (big_rej) phase_reject<Team, F32, 8>(T, S, gam, 0, b, r, S.C, nullptr);
+      else phase_reject<Team, F32, 1>(T, S, gam, 0, b, r, S.C, nullptr);
       // CTAs beyond the rejection items take the a-priori errors and the previous call's
       // deferred P/u update
       const long long nrej = (long long)((b + 4 * (big_rej ? 8 : 1) - 1) / (4 * (big_rej ? 8 : 1))) * S.nmc;
       const int w_lo = (int)min(nrej, (long long)max(0, T.size() - 16));
       phase_dall(T, S, A, j0, b, r, w_lo);
-      if (sh[4] > 0) acc_rows<Team, MIXED>(T, S, S.Gpend, S.Dpend, 0, sh[4], r, w_lo);
+      if (sh[4] > 0) acc_rows<Team, F32>(T, S, S.Gpend, S.Dpend, 0, sh[4], r, w_lo);
       if (!T.sync()) return false;
       // 3: decide
       if (b <= SMALL_B) {
-        q0 = decide_rows<MIXED>(S, A, j0, b, r, T.id() == 0);
+        q0 = decide_rows<F32>(S, A, j0, b, r, T.id() == 0);
         if (q0 == b) {  // fast finish: every row dependent
           const bool defer = S.defer && last && j0 == 0;  // the call's only block
-          if (!defer) acc_small<Team, MIXED>(T, S, 0, b, r);
+          if (!defer) acc_small<Team, F32>(T, S, 0, b, r);
           if (T.id() == 0) {
             if (A.indep)
               for (int j = threadIdx.x; j < b; j += NT) A.indep[j0 + j] = 0;
@@ -1246,7 +1247,7 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
           continue;
         }
       } else {
-        decide_rows_team<Team, MIXED>(T, S, A, j0, b, r);
+        decide_rows_team<Team, F32>(T, S, A, j0, b, r);
         if (!T.sync()) return false;
         if (threadIdx.x == 0) sh[3] = __ldcg(S.ctrl + CTRL_Q0);
         __syncthreads();
@@ -1254,19 +1255,19 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       }
     }
     // 4: dependent run before the first special row
-    if (q0 > 0 && !dep_run<Team, MIXED>(T, S, 0, q0, r)) return false;
+    if (q0 > 0 && !dep_run<Team, F32>(T, S, 0, q0, r)) return false;
     int applied = b, rnew = r;
     if (q0 < b) {
       // 5: sequential section, in FP64 (rows [q0, bend)); its rows never overlap the run
       const int bend = min(b, q0 + SLOW_MAX);
       if ((long long)((bend - q0 + 7) / 8) * r < 4LL * NWARP * T.size())
-        phase_gamma_cta(T, S, gam, q0, bend, r, MIXED ? S.C : S.Ct);
+        phase_gamma_cta(T, S, gam, q0, bend, r, ORTHO ? S.C : S.Ct);
       else
-        phase_gamma<Team, false>(T, S, gam, q0, bend, r, MIXED ? S.C : S.Ct);
+        phase_gamma<Team, false>(T, S, gam, q0, bend, r, ORTHO ? S.C : S.Ct);
       if (!T.sync()) return false;
       phase_reject<Team, false, 1>(T, S, gam, q0, bend, r, S.C, S.R);
       if (!T.sync()) return false;
-      if (!scan_team<Team, MIXED>(T, S, A, j0, q0, bend, r)) return false;
+      if (!scan_team<Team, ORTHO>(T, S, A, j0, q0, bend, r)) return false;
       // the scan may have used the dynamic shared memory that caches the tensor-core B tiles
       if (S.tcx && threadIdx.x == 0) reinterpret_cast<TcCtx*>(S.tcx)->cq = nullptr;
       if (!T.sync()) return false;
@@ -1279,8 +1280,8 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       applied = sh[5];
       rnew = sh[6];
       const int nind = sh[7];
-      section_apply_pu<Team, MIXED>(T, S, q0, applied - q0, r, rnew);
-      if (nind > 0) section_apply_basis<Team, MIXED>(T, S, A, j0, r, nind);
+      section_apply_pu<Team, ORTHO>(T, S, q0, applied - q0, r, rnew);
+      if (nind > 0) section_apply_basis<Team, ORTHO>(T, S, A, j0, r, nind);
     }
     // finalize the block (worker 0): flags, counters, rank, next block size
     if (T.id() == 0) {

@@ -76,8 +76,12 @@ struct rg_state {
   void* arena = nullptr;  // one device allocation for everything
   size_t arena_bytes = 0;
   // staging for the host-buffer entry points (allocated on first use)
-  double* stage = nullptr;
+  double* stage = nullptr;  // two slots of stage_rows rows (and targets) each
   uint8_t* stage_ind = nullptr;
+  cudaStream_t copy_stream = nullptr;  // host-to-device copies of the host entry point
+  cudaEvent_t copied[2] = {nullptr, nullptr};    // slot s holds the rows of its latest copy
+  cudaEvent_t consumed[2] = {nullptr, nullptr};  // the call that read slot s has finished
+  int slot = 0;
   long long stage_rows = 0;
   double* xbuf = nullptr;
   // two small (SMALL_B-row) gamma / a-priori-error buffers used alternately by calls of at
@@ -108,7 +112,7 @@ size_t carve(StreamDev& S, char* base, double** gs = nullptr, double** ds = null
   Carver cv{base};
   const size_t ld = (size_t)S.ld, rm = (size_t)S.r_max, kb = (size_t)S.kb_max;
   S.C = cv.take<double>(rm * ld);
-  S.Ct = S.mixed ? nullptr : cv.take<double>(rm * ld);
+  S.Ct = S.ortho ? nullptr : cv.take<double>(rm * ld);
   S.Qf = S.mixed ? cv.take<float>(rm * ld) : nullptr;
   S.Pinv = cv.take<double>(rm * rm);
   S.P = cv.take<double>(rm * rm);
@@ -207,7 +211,7 @@ rg_status rg_init(rg_state** out, int64_t m, double tol, int flags, int64_t r_ma
   *out = nullptr;
   if (m <= 0 || m > (1 << 24)) return fail(RG_EINVAL, "rg_init: m = %lld out of range", (long long)m);
   if (std::isnan(tol)) return fail(RG_EINVAL, "rg_init: tol is NaN");
-  if (flags & ~(RG_MIXED | RG_TEST_PAPER)) return fail(RG_EINVAL, "rg_init: unknown flags %d", flags);
+  if (flags & ~(RG_MIXED | RG_TEST_PAPER | RG_ORTHONORMAL)) return fail(RG_EINVAL, "rg_init: unknown flags %d", flags);
   if (r_max <= 0 || r_max > m) r_max = m;
   rg_state* st = new (std::nothrow) rg_state();
   if (!st) return fail(RG_ENOMEM, "rg_init: host allocation failed");
@@ -222,6 +226,7 @@ rg_status rg_init(rg_state** out, int64_t m, double tol, int flags, int64_t r_ma
   S.ld = (int)align_up((size_t)m, 4);
   S.r_max = (int)r_max;
   S.mixed = (flags & RG_MIXED) ? 1 : 0;
+  S.ortho = (flags & (RG_MIXED | RG_ORTHONORMAL)) ? 1 : 0;
   S.test_mode = (flags & RG_TEST_PAPER) ? 2 : 0;
   S.tol = tol;
   S.tau_lo = 1e-5;
@@ -241,7 +246,7 @@ rg_status rg_init(rg_state** out, int64_t m, double tol, int flags, int64_t r_ma
     return cuda_fail(e, "rg_init: cudaMalloc of the state");
   }
   carve(S, (char*)st->arena, st->Gs, st->Ds);
-  e = stream_grid_size(S.mixed, &st->grid);
+  e = stream_grid_size(S.mixed, S.ortho, &st->grid);
   if (e != cudaSuccess || st->grid <= 0) {
     cudaFree(st->arena);
     delete st;
@@ -283,30 +288,50 @@ rg_status rg_add_rows_host(rg_state* st, const double* Gamma, const double* y, i
   if (!Gamma || !y) return fail(RG_EINVAL, "rg_add_rows_host: NULL rows or targets");
   const long long m = st->S.m;
   if (!st->stage) {
-    long long rows = std::max<long long>(1, (64ll << 20) / (8 * (m + 1)));
-    cudaError_t e = cudaMalloc(&st->stage, (size_t)rows * (size_t)(m + 1) * 8);
+    long long rows = std::max<long long>(1, (32ll << 20) / (8 * (m + 1)));
+    cudaError_t e = cudaMalloc(&st->stage, 2 * (size_t)rows * (size_t)(m + 1) * 8);
     if (e == cudaSuccess) e = cudaMalloc(&st->stage_ind, (size_t)rows);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st->copy_stream, cudaStreamNonBlocking);
+    for (int h = 0; h < 2 && e == cudaSuccess; ++h) {
+      e = cudaEventCreateWithFlags(&st->copied[h], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->consumed[h], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(st->consumed[h], st->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "rg_add_rows_host: staging allocation");
     st->stage_rows = rows;
   }
+  // Two staging slots: the rows of one chunk are copied on the copy stream while the
+  // previous chunk's (or call's) update runs on the state's stream; a slot is refilled
+  // only after the update that read it has finished. The call returns once its last copy
+  // is done (the host buffers may then be reused); the update itself is asynchronous
+  // unless indep_out is requested.
+  cudaError_t e = cudaSuccess;
+  int last = -1;
   for (long long c0 = 0; c0 < k; c0 += st->stage_rows) {
     const long long n = std::min(st->stage_rows, (long long)k - c0);
-    double* dG = st->stage;
-    double* dy = st->stage + (size_t)st->stage_rows * (size_t)m;
-    cudaError_t e = cudaMemcpyAsync(dG, Gamma + (size_t)c0 * m, (size_t)n * m * 8,
-                                    cudaMemcpyHostToDevice, st->stream);
+    const int h = st->slot;
+    st->slot ^= 1;
+    double* dG = st->stage + (size_t)h * st->stage_rows * (size_t)(m + 1);
+    double* dy = dG + (size_t)st->stage_rows * (size_t)m;
+    e = cudaStreamWaitEvent(st->copy_stream, st->consumed[h], 0);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(dy, y + c0, (size_t)n * 8, cudaMemcpyHostToDevice, st->stream);
+      e = cudaMemcpyAsync(dG, Gamma + (size_t)c0 * m, (size_t)n * m * 8, cudaMemcpyHostToDevice, st->copy_stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dy, y + c0, (size_t)n * 8, cudaMemcpyHostToDevice, st->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(st->copied[h], st->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st->stream, st->copied[h], 0);
     if (e != cudaSuccess) return cuda_fail(e, "rg_add_rows_host: copy to device");
     rg_status s = rg_add_rows(st, dG, dy, n, indep_out ? st->stage_ind : nullptr);
     if (s != RG_OK) return s;
-    if (indep_out) {
-      e = cudaMemcpyAsync(indep_out + c0, st->stage_ind, (size_t)n, cudaMemcpyDeviceToHost,
-                          st->stream);
-      if (e != cudaSuccess) return cuda_fail(e, "rg_add_rows_host: copy to host");
+    e = cudaEventRecord(st->consumed[h], st->stream);
+    if (e == cudaSuccess && indep_out) {
+      e = cudaMemcpyAsync(indep_out + c0, st->stage_ind, (size_t)n, cudaMemcpyDeviceToHost, st->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);  // stage_ind is reused
     }
+    if (e != cudaSuccess) return cuda_fail(e, "rg_add_rows_host: copy to host");
+    last = h;
   }
-  cudaError_t e = cudaStreamSynchronize(st->stream);
+  if (last >= 0) e = cudaEventSynchronize(st->copied[last]);
   if (e != cudaSuccess) return cuda_fail(e, "rg_add_rows_host: synchronise");
   return RG_OK;
 }
@@ -450,11 +475,24 @@ rg_status rg_set_stream(rg_state* st, void* cuda_stream) {
   return RG_OK;
 }
 
+rg_status rg_set_screen(rg_state* st, double tau_lo) {
+  if (!valid_state(st)) return fail(RG_EINVAL, "rg_set_screen: invalid state");
+  if (!(tau_lo > 0.0 && tau_lo < 1.0)) return fail(RG_EINVAL, "rg_set_screen: tau_lo = %g outside (0, 1)", tau_lo);
+  st->S.tau_lo = tau_lo;
+  return RG_OK;
+}
+
 rg_status rg_free(rg_state* st) {
   if (!st) return RG_OK;
   cudaStreamSynchronize(st->stream);
+  if (st->copy_stream) cudaStreamSynchronize(st->copy_stream);
   if (st->arena) cudaFree(st->arena);
   if (st->stage) cudaFree(st->stage);
+  for (int h = 0; h < 2; ++h) {
+    if (st->copied[h]) cudaEventDestroy(st->copied[h]);
+    if (st->consumed[h]) cudaEventDestroy(st->consumed[h]);
+  }
+  if (st->copy_stream) cudaStreamDestroy(st->copy_stream);
   if (st->stage_ind) cudaFree(st->stage_ind);
   if (st->xbuf) cudaFree(st->xbuf);
   delete st;

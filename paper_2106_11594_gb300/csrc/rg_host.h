@@ -17,7 +17,7 @@ rg_status status_from_bits(int bits);
 
 cudaError_t launch_stream(const StreamDev& S, const double* Gamma, const double* y, long long k,
                           uint8_t* indep, int grid, cudaStream_t stream);
-cudaError_t stream_grid_size(int mixed, int* grid);
+cudaError_t stream_grid_size(int mixed, int ortho, int* grid);
 cudaError_t launch_export_prep(const StreamDev& S, int grid, cudaStream_t stream);
 cudaError_t launch_flush(const StreamDev& S, int grid, cudaStream_t stream);
 cudaError_t launch_solution(const StreamDev& S, double* X, cudaStream_t stream);

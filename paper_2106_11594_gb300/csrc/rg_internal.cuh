@@ -43,14 +43,15 @@ enum : int {
 
 // Everything a kernel needs to know about one stream. Plain pointers into device
 // memory owned by the host-side rg_state. Two algebraic variants:
-//  * general (FP64 mode): C = selected observation rows, Ct = dual basis
+//  * general (FP64 mode by default): C = selected observation rows, Ct = dual basis
 //    (Ct C^T = I), Algorithm 1 of the paper;
-//  * orthonormal (mixed mode): C = Q with orthonormal rows spanning the same space
-//    (Section 2.2, alpha = 1/||Gamma_r||), so the dual basis is Q itself; a FP32 copy
-//    Qf feeds the FP32 projections.
+//  * orthonormal (mixed mode, or FP64 mode on request): C = Q with orthonormal rows
+//    spanning the same space (Section 2.2, alpha = 1/||Gamma_r||), so the dual basis is
+//    Q itself; in mixed mode an FP32 copy Qf feeds the FP32 projections.
 struct StreamDev {
   int m, ld, r_max, kb_max;
-  int mixed;      // 1: orthonormal variant with FP32 projections
+  int mixed;      // 1: FP32 projections (implies the orthonormal variant)
+  int ortho;      // 1: orthonormal variant
   int test_mode;  // 0 REL, 2 PAPER
   double tol;     // <= 0: paper default (m^2 r + m r + m) eps_M
   double tau_lo;  // mixed mode: FP32 relative-rejection floor below which rows are dependent

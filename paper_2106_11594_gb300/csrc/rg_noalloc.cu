@@ -34,7 +34,7 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {};
-int g_noalloc_grid[2][kMaxDevices] = {};
+int g_noalloc_grid[kMaxDevices] = {};
 
 size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -49,7 +49,7 @@ size_t noalloc_layout(StreamDev& S, char* base) {
   };
   const size_t ld = (size_t)S.ld, rm = (size_t)S.r_max, kb = (size_t)S.kb_max;
   S.C = (double*)take(rm * ld * 8);
-  S.Ct = S.mixed ? nullptr : (double*)take(rm * ld * 8);
+  S.Ct = S.ortho ? nullptr : (double*)take(rm * ld * 8);
   S.Qf = S.mixed ? (float*)take(rm * ld * 4) : nullptr;
   S.Pinv = nullptr;
   S.P = (double*)take(rm * rm * 8);
@@ -85,10 +85,16 @@ size_t noalloc_layout(StreamDev& S, char* base) {
 
 }  // namespace
 
-template <bool MIXED>
+template <bool F32, bool ORTHO>
 __global__ void __launch_bounds__(NT, 1) noalloc_kernel(StreamDev S, CallArgs A) {
   grid_barrier_init(S.ctrl);
-  process_rows<GridTeam, MIXED>(GridTeam{S.ctrl}, S, A);
+  process_rows<GridTeam, F32, ORTHO>(GridTeam{S.ctrl}, S, A);
+}
+
+// FP32 projections always come with the orthonormal variant.
+static const void* noalloc_kernel_ptr(int mixed, int ortho) {
+  if (mixed) return (const void*)noalloc_kernel<true, true>;
+  return ortho ? (const void*)noalloc_kernel<false, true> : (const void*)noalloc_kernel<false, false>;
 }
 
 // Clears what must start at zero before each call: the control words (rank, status,
@@ -106,7 +112,7 @@ __global__ void noalloc_reset_kernel(int* ctrl, long long* rows_seen, int kb0) {
 __global__ void __launch_bounds__(NT, 1) noalloc_solution_kernel(StreamDev S, double* X) {
   const int r = S.ctrl[CTRL_R];
   form_w(S, r);
-  const double* B = S.mixed ? S.C : S.Ct;
+  const double* B = S.ortho ? S.C : S.Ct;
   for (int c = threadIdx.x; c < S.m; c += NT) {
     double acc = 0.0;
     for (int i = 0; i < r; ++i) acc = fma(__ldcg(B + (size_t)i * S.ld + c), __ldcg(S.w + i), acc);
@@ -125,13 +131,15 @@ extern "C" rg_status rg_solve_noalloc(const double* Gamma, const double* y, int6
   if (n < 0) return fail(RG_EINVAL, "rg_solve_noalloc: n = %lld < 0", (long long)n);
   if ((n > 0 && (!Gamma || !y)) || !X) return fail(RG_EINVAL, "rg_solve_noalloc: NULL buffer");
   if (std::isnan(tol)) return fail(RG_EINVAL, "rg_solve_noalloc: tol is NaN");
-  if (flags & ~(RG_MIXED | RG_TEST_PAPER)) return fail(RG_EINVAL, "rg_solve_noalloc: unknown flags %d", flags);
+  if (flags & ~(RG_MIXED | RG_TEST_PAPER | RG_ORTHONORMAL))
+    return fail(RG_EINVAL, "rg_solve_noalloc: unknown flags %d", flags);
   if (r_max <= 0 || r_max > m) r_max = m;
   StreamDev S{};
   S.m = (int)m;
   S.ld = (int)((m + 3) / 4 * 4);
   S.r_max = (int)r_max;
   S.mixed = (flags & RG_MIXED) ? 1 : 0;
+  S.ortho = (flags & (RG_MIXED | RG_ORTHONORMAL)) ? 1 : 0;
   S.test_mode = (flags & RG_TEST_PAPER) ? 2 : 0;
   S.tol = tol;
   S.tau_lo = 1e-5;
@@ -161,20 +169,18 @@ extern "C" rg_status rg_solve_noalloc(const double* Gamma, const double* y, int6
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess) return cuda_fail(e, "rg_solve_noalloc: cudaGetSymbolAddress");
-      int nsm = 0, per0 = 0, per1 = 0;
+      int nsm = 0, per[3] = {0, 0, 0};
       e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per0, noalloc_kernel<false>, NT, 0);
-      if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, noalloc_kernel<true>, NT, 0);
+      for (int v = 0; v < 3 && e == cudaSuccess; ++v)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[v], noalloc_kernel_ptr(v == 2, v >= 1), NT, 0);
       if (e != cudaSuccess) return cuda_fail(e, "rg_solve_noalloc: occupancy query");
-      if (per0 < 1 || per1 < 1) return fail(RG_ECUDA, "rg_solve_noalloc: kernel cannot be resident");
-      g_noalloc_grid[0][dev] = std::min(nsm, 1024);
-      g_noalloc_grid[1][dev] = std::min(nsm, 1024);
+      if (per[0] < 1 || per[1] < 1 || per[2] < 1)
+        return fail(RG_ECUDA, "rg_solve_noalloc: kernel cannot be resident");
+      g_noalloc_grid[dev] = std::min(nsm, 1024);
       g_noalloc_ptr[dev] = p;
     }
     base = g_noalloc_ptr[dev];
-    grid = g_noalloc_grid[S.mixed][dev];
+    grid = g_noalloc_grid[dev];
   }
   noalloc_layout(S, (char*)base);
   cudaStream_t stream = (cudaStream_t)cuda_stream;
@@ -184,9 +190,8 @@ extern "C" rg_status rg_solve_noalloc(const double* Gamma, const double* y, int6
   if (n > 0) {
     CallArgs A{Gamma, y, n, nullptr};
     void* args[] = {(void*)&S, (void*)&A};
-    e = cudaLaunchCooperativeKernel(
-        S.mixed ? (const void*)noalloc_kernel<true> : (const void*)noalloc_kernel<false>,
-        dim3(grid), dim3(NT), args, 0, stream);
+    e = cudaLaunchCooperativeKernel(noalloc_kernel_ptr(S.mixed, S.ortho), dim3(grid), dim3(NT), args, 0,
+                                    stream);
     if (e != cudaSuccess) return cuda_fail(e, "rg_solve_noalloc: launch");
   }
   noalloc_solution_kernel<<<1, NT, 0, stream>>>(S, X);

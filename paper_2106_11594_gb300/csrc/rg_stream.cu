@@ -42,10 +42,10 @@
 
 namespace rg {
 
-template <bool MIXED>
+template <bool F32, bool ORTHO>
 __global__ void __launch_bounds__(NT, 1) stream_kernel(StreamDev S, CallArgs A) {
   grid_barrier_init(S.ctrl);
-  process_rows<GridTeam, MIXED>(GridTeam{S.ctrl}, S, A);
+  process_rows<GridTeam, F32, ORTHO>(GridTeam{S.ctrl}, S, A);
 }
 
 // Folds the P/u update deferred by the last small call (if any) into P and u: every CTA
@@ -66,7 +66,7 @@ __global__ void solution_kernel(StreamDev S, double* X) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= S.m) return;
   const int r = S.ctrl[CTRL_R];
-  const double* B = S.mixed ? S.C : S.Ct;
+  const double* B = S.ortho ? S.C : S.Ct;
   double acc = 0.0;
   for (int i = 0; i < r; ++i) acc = fma(B[(size_t)i * S.ld + c], S.w[i], acc);
   X[c] = acc;
@@ -93,7 +93,7 @@ __global__ void export_kernel(StreamDev S, double* C, double* Ct, double* Pinv, 
   for (long long e = tid; e < nm; e += str) {
     const int i = (int)(e / S.m), c = (int)(e - (long long)i * S.m);
     if (C) C[e] = S.C[(size_t)i * S.ld + c];
-    if (Ct) Ct[e] = S.mixed ? S.C[(size_t)i * S.ld + c] : S.Ct[(size_t)i * S.ld + c];
+    if (Ct) Ct[e] = S.ortho ? S.C[(size_t)i * S.ld + c] : S.Ct[(size_t)i * S.ld + c];
   }
   for (long long e = tid; e < (long long)r * r; e += str) {
     const int i = (int)(e / r), l = (int)(e - (long long)i * r);
@@ -106,26 +106,28 @@ __global__ void export_kernel(StreamDev S, double* C, double* Ct, double* Pinv, 
 }
 
 // Host-side launch helpers (declared in rg_host.h).
+// FP32 projections always come with the orthonormal variant.
+static const void* stream_kernel_ptr(int mixed, int ortho) {
+  if (mixed) return (const void*)stream_kernel<true, true>;
+  return ortho ? (const void*)stream_kernel<false, true> : (const void*)stream_kernel<false, false>;
+}
+
 cudaError_t launch_stream(const StreamDev& S, const double* Gamma, const double* y, long long k,
                           uint8_t* indep, int grid, cudaStream_t stream) {
   CallArgs A{Gamma, y, k, indep};
   StreamDev Sc = S;
   void* args[] = {(void*)&Sc, (void*)&A};
-  if (S.mixed)
-    return cudaLaunchCooperativeKernel((const void*)stream_kernel<true>, dim3(grid), dim3(NT),
-                                       args, 0, stream);
-  return cudaLaunchCooperativeKernel((const void*)stream_kernel<false>, dim3(grid), dim3(NT),
+  return cudaLaunchCooperativeKernel(stream_kernel_ptr(S.mixed, S.ortho), dim3(grid), dim3(NT),
                                      args, 0, stream);
 }
 
-cudaError_t stream_grid_size(int mixed, int* grid) {
+cudaError_t stream_grid_size(int mixed, int ortho, int* grid) {
   int dev = 0, nsm = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per, mixed ? (const void*)stream_kernel<true> : (const void*)stream_kernel<false>, NT, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stream_kernel_ptr(mixed, ortho), NT, 0);
   if (e != cudaSuccess) return e;
   *grid = std::min(nsm, 1024) * (per >= 1 ? 1 : 0);  // the section scan holds <= 1024 workers
   return cudaSuccess;

@@ -16,6 +16,7 @@ from . import build as _build
 RG_OK, RG_EINVAL, RG_ENOMEM, RG_ECUDA, RG_ECAPACITY, RG_ENONFINITE, RG_ETIMEOUT = range(7)
 RG_FP64, RG_MIXED = 0, 1
 RG_TEST_REL, RG_TEST_PAPER = 0, 2
+RG_ORTHONORMAL = 4  # the orthonormal variant (Section 2.2); implied by RG_MIXED
 
 STATUS_NAMES = {0: "RG_OK", 1: "RG_EINVAL", 2: "RG_ENOMEM", 3: "RG_ECUDA", 4: "RG_ECAPACITY",
                 5: "RG_ENONFINITE", 6: "RG_ETIMEOUT"}
@@ -68,6 +69,8 @@ def lib(build: bool = True):
         "rg_adjoint": [vp, vp, vp, i64, vp, vp, vp, vp],
         "rg_batch_adjoint": [vp, vp, vp, vp, vp, i64, vp, vp, vp, vp],
         "rg_batch_set_stream": [vp, vp],
+        "rg_set_screen": [vp, f64],
+        "rg_batch_set_screen": [vp, f64],
         "rg_batch_set_block_rows": [vp, i64, vp],
     }
     for name, args in sig.items():
@@ -157,6 +160,10 @@ class RankGreville:
         _check(lib().rg_adjoint(self._h, _ptr(A), _ptr(y), int(A.shape[0]), _ptr(g), _ptr(gA),
                                 _ptr(gy), _ptr(X)), "rg_adjoint")
 
+    def set_screen(self, tau_lo: float):
+        """rg_set_screen: floor of mixed mode's FP32 screen."""
+        _check(lib().rg_set_screen(self._h, float(tau_lo)), "rg_set_screen")
+
     def solution_host(self, X):
         r = ctypes.c_int64(0)
         _check(lib().rg_solution_host(self._h, _ptr(X), ctypes.byref(r)), "rg_solution_host")
@@ -239,6 +246,10 @@ class RankGrevilleBatch:
         """Issue later calls on `stream` (default: torch's current stream), e.g. inside
         torch.cuda.graph capture."""
         _check(lib().rg_batch_set_stream(self._h, _stream(stream)), "rg_batch_set_stream")
+
+    def set_screen(self, tau_lo: float):
+        """rg_batch_set_screen: floor of mixed mode's FP32 screen."""
+        _check(lib().rg_batch_set_screen(self._h, float(tau_lo)), "rg_batch_set_screen")
 
     def block_rows(self, rows: int = 0) -> int:
         """Set (rows > 0) and/or return the per-block row cap (rg_batch_set_block_rows)."""

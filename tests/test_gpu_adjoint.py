@@ -22,7 +22,8 @@ def _case(n, m, r, seed):
     return A, y, g
 
 
-@pytest.mark.parametrize("mode,tol", [(rg.RG_FP64, 1e-9), (rg.RG_MIXED, 1e-3)])
+@pytest.mark.parametrize("mode,tol", [(rg.RG_FP64, 1e-9), (rg.RG_FP64 | rg.RG_ORTHONORMAL, 1e-9),
+                                      (rg.RG_MIXED, 1e-3)])
 def test_adjoint_matches_oracle(mode, tol):
     torch, dev = torch_cuda()
     from paper_2106_11594_gb300.autograd import lstsq_rg

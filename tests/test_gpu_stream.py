@@ -249,3 +249,67 @@ def test_solutions_and_exports_between_calls_of_mixed_sizes(mode, tol):
             assert checks.rel_err(X.cpu().numpy(), o.X) <= tol, (c, j0)
     assert j0 == s.n
     st.close()
+
+
+def test_ill_conditioned_rank_growth():
+    """Workload 5 at reduced size (n 4096, m 512, r 64; singular values log-uniform on
+    [1e-6, 1], 8 rank-growth phases, 5% combinations of earlier rows), tol 1e-8.
+
+    The method projects with one classical Gram-Schmidt pass and no reorthogonalisation
+    (Section 2.2; Section 4.2 finds it neither forward nor mixed stable). As directions
+    with small relative rejections are appended, the orthonormal basis loses
+    orthogonality and the general variant's dual basis loses accuracy, until the
+    rounding noise in a dependent row's rejection exceeds tol and every later row is
+    declared independent. The oracle follows the generator's rank growth up to a row d
+    (past phase 0 here); over that prefix the GPU must take the oracle's decisions and
+    reach an X as close to the exact solution as the oracle's. Past d both runs decide
+    on rounding noise, so the full stream only checks what holds for any run: a run that
+    completes ends at or above the generator's rank, and a run that stops does so by the
+    capacity stop at rank m or by the breakdown check."""
+    s = inputs.ill_conditioned_stream(n=4096, m=512, r=64)
+    tol = 1e-8
+    torch, dev = torch_cuda()
+    for mode, variant in ((rg.RG_FP64, fp64.GENERAL), (rg.RG_MIXED, fp64.ORTHONORMAL)):
+        o = fp64.solve(s.A, s.Y, tol=tol, variant=variant)
+        d = int(np.flatnonzero(o.indep != s.growth)[0])
+        assert d >= 512, d  # the oracle holds the generator's rank growth through phase 0
+        od = fp64.solve(s.A[:d], s.Y[:d], tol=tol, variant=variant)
+        for n_run in (d, s.n):
+            At = torch.from_numpy(s.A[:n_run]).to(dev)
+            Yt = torch.from_numpy(s.Y[:n_run]).to(dev)
+            st = rg.RankGreville(512, tol, mode)
+            if mode == rg.RG_MIXED:
+                st.set_screen(1e-9)  # below the smallest relative rejection of a new direction
+            ind = torch.zeros(n_run, dtype=torch.uint8, device=dev)
+            for j0 in range(0, n_run, 256):
+                st.add_rows(At[j0:j0 + 256], Yt[j0:j0 + 256], ind[j0:j0 + 256])
+            X = torch.empty(512, dtype=torch.float64, device=dev)
+            try:
+                rank = st.solution(X)
+            except rg.RGError as e:
+                # past d the noise can declare a row independent at rank m (the stream
+                # stops with RG_ECAPACITY, as the oracle does), or the noisy state can make
+                # a Woodbury denominator non-positive (the breakdown check stops it with
+                # RG_ENONFINITE); either way the rows from there on are not applied
+                assert n_run == s.n and e.code in (rg.RG_ECAPACITY, rg.RG_ENONFINITE), (mode, e)
+                rank = st.rank()
+                assert o.status == 4
+                assert rank == 512 or e.code == rg.RG_ENONFINITE
+            got = ind.cpu().numpy()
+            st.close()
+            np.testing.assert_array_equal(got[:d], od.indep)
+            if n_run == d:
+                # The method is not forward stable (Section 4.2): on this prefix the
+                # oracle itself is far from the exact minimum-norm solution (Xs, by SVD
+                # at the prefix rank). The GPU run of the same method must land no
+                # further from Xs than ten times the oracle's own error.
+                assert rank == od.rank
+                U, sv, Vt = np.linalg.svd(s.A[:d], full_matrices=False)
+                r = od.rank
+                Xs = Vt[:r].T @ ((U[:, :r].T @ s.Y[:d]) / sv[:r])
+                floor = TOL64 if mode == rg.RG_FP64 else TOLMIX
+                err_o = checks.rel_err(od.X, Xs)
+                err_g = checks.rel_err(X.cpu().numpy(), Xs)
+                assert err_g <= max(floor, 10 * err_o), (err_g, err_o)
+            else:
+                assert rank >= s.rank
