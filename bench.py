@@ -41,8 +41,8 @@ WORKLOAD = f"single FP64 stream n={N_ROWS} m={M} r={R}, k={K_CALL} rows per rg_a
 # DRAM bytes (read + write) of one 32-row stream_kernel<false, false> launch, from the ncu capture
 # summarised in profiles/stream_kernel_fp64_k32_n4096_full.md, and the hash of the kernel
 # sources it was taken on: once the sources change the figure no longer applies (null).
-TRAFFIC_BYTES_PER_LAUNCH = 1465856
-TRAFFIC_SOURCES_SHA = "5924edff81577ad4"
+TRAFFIC_BYTES_PER_LAUNCH = 1466112
+TRAFFIC_SOURCES_SHA = "af0a40fdb77a71da"
 
 
 STREAM_KERNEL_SOURCES = ("rg_stream.cu", "rg_core.cuh", "rg_internal.cuh", "rg_tc.cuh")
@@ -173,12 +173,15 @@ def run_gpu(args):
 
     def one_step(st, k, ev=None):
         st.reset()
-        for j0 in range(0, n, k):
-            if ev is not None:
+        for c, j0 in enumerate(range(0, n, k)):
+            # launch durations are sampled on every 16th call: an event pair around every
+            # launch would itself slow the timed region by ~15 %
+            sample = ev is not None and c % 16 == 0
+            if sample:
                 ev[0].append(torch.cuda.Event(enable_timing=True))
                 ev[0][-1].record(stream)
             st.add_rows(A[j0:j0 + k], Y[j0:j0 + k])
-            if ev is not None:
+            if sample:
                 ev[1].append(torch.cuda.Event(enable_timing=True))
                 ev[1][-1].record(stream)
         st.solution(X, with_rank=False)
