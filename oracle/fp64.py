@@ -54,6 +54,9 @@ def lib():
             L.rgo_solve_batch.argtypes = [i64, i64p, i64p, i64p, f64p, f64p, ctypes.c_double,
                                           ctypes.c_int, ctypes.c_int, f64p, i64p, ctypes.c_void_p]
             L.rgo_solve_batch.restype = ctypes.c_int
+            L.rgo_pinv_mut.argtypes = [i64, i64, f64p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                       f64p, i64p, u8p]
+            L.rgo_pinv_mut.restype = ctypes.c_int
             L.rgo_max_threads.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -105,6 +108,21 @@ def solve(A, Y, tol: float = 1e-10, test_mode: int = TEST_REL, r_max: int = 0,
     return Result(X=X, rank=r, basis_rows=basis[:r].copy(), indep=indep[:n].copy(),
                   Ct=Ct[:r * m].reshape(r, m).copy(), Pinv=Pinv[:r * r].reshape(r, r).copy(),
                   C=C[:r * m].reshape(r, m).copy(), rows_done=int(done[0]), status=st)
+
+
+def pinv(A, tol: float = 1e-10, test_mode: int = TEST_REL, mutation: int = 0):
+    """Pseudoinverse update of Theorems label_th_pinv_indep / label_th_pinv_lindep over the
+    rows of A (n x m): returns (A^+ as an m x n array, rank, per-row independence flags)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n, m = A.shape
+    Ap = np.zeros(m * max(n, 1))
+    rank = np.zeros(1, dtype=np.int64)
+    indep = np.zeros(max(n, 1), dtype=np.uint8)
+    st = lib().rgo_pinv_mut(n, m, _ptr(A), float(tol), int(test_mode), int(mutation), _ptr(Ap),
+                            _ptr(rank), _ptr(indep))
+    if st != 0:
+        raise RuntimeError(f"rgo_pinv failed with status {st}")
+    return Ap[:m * n].reshape(m, n).copy(), int(rank[0]), indep[:n].copy()
 
 
 def solve_batch(A_packed, Y_packed, row_off, elem_off, x_off, tol: float = 1e-10,

@@ -280,6 +280,92 @@ int rgo_solve(int64_t n, int64_t m, const double *A, const double *Y, double tol
 }
 
 /*
+ * Pseudoinverse update (Theorems label_th_pinv_indep and label_th_pinv_lindep): feed the
+ * n rows of A (n x m, row-major) in order and keep A_n^+ (m x n) explicitly. Per row,
+ * with the general factorization of Algorithm 1 before the row (C, Ct, P^-1 and B_n):
+ *   gamma = Ct Gamma, zeta = P^-1 gamma, b = B_n zeta (Eq. label_eq_znplusone),
+ *   K = Gamma_r / ||Gamma_r||^2 (independent) or Ct^T zeta / (1 + gamma^T zeta)
+ *   (dependent), exactly the K of Algorithm 1 (rgo_update forms it),
+ *   A_{n+1}^+ = [A_n^+ - K b^T, K],
+ * and B grows as the factorizations of the two theorems' proofs state:
+ *   dependent: B_{n+1} = [B_n; gamma^T]; independent: B_{n+1} = [[B_n, 0], [0, 1]].
+ * Output Apinv (m x n row-major: Apinv[c * n + i] is entry (c, i) of A^+); rank_out and
+ * indep (n) may be NULL. mutation plants a mistake for the pins: 10 drops the -K b^T
+ * term, 11 adds it with the wrong sign, 12 appends gamma^T to B for an independent row.
+ * Returns 0, 1 (bad arguments), 2 (out of memory) or 4 (a row would make the rank exceed m).
+ */
+int rgo_pinv_mut(int64_t n, int64_t m, const double *A, double tol, int test_mode, int mutation,
+                 double *Apinv, int64_t *rank_out, uint8_t *indep) {
+  if (n < 0 || m <= 0 || (n > 0 && !A) || !Apinv || tol != tol) return 1;
+  const int64_t r_max = m;
+  rgo_state sto;
+  rgo_state *st = &sto;
+  double *Bm = (double *)calloc((size_t)((n > 0 ? n : 1) * r_max), sizeof(double));
+  double *gam = (double *)calloc((size_t)r_max + 1, sizeof(double));
+  double *zet = (double *)calloc((size_t)r_max + 1, sizeof(double));
+  double *b = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  if (rgo_alloc(st, m, r_max, tol, test_mode) || !Bm || !gam || !zet || !b) {
+    rgo_release(st);
+    free(Bm); free(gam); free(zet); free(b);
+    return 2;
+  }
+  for (int64_t e = 0; e < m * n; ++e) Apinv[e] = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double *G = A + i * m;
+    const int64_t r = st->r;
+    /* gamma = Ct Gamma, zeta = P^-1 gamma, b = B_n zeta (state before the row) */
+    for (int64_t k = 0; k < r; ++k) {
+      double acc = 0.0;
+      for (int64_t c = 0; c < m; ++c) acc += CT(k, c) * G[c];
+      gam[k] = acc;
+    }
+    for (int64_t k = 0; k < r; ++k) {
+      double acc = 0.0;
+      for (int64_t l = 0; l < r; ++l) acc += st->Pinv[k * st->r_max + l] * gam[l];
+      zet[k] = acc;
+    }
+    for (int64_t j = 0; j < i; ++j) {
+      double acc = 0.0;
+      for (int64_t k = 0; k < r; ++k) acc += Bm[j * r_max + k] * zet[k];
+      b[j] = acc;
+    }
+    /* Algorithm 1 on the row: decides it, forms K and updates C, Ct, P^-1 */
+    int res = rgo_update(st, G, 0.0);
+    if (res < 0) { /* rank would exceed m: only a breakdown of the rank test gets here */
+      rgo_release(st);
+      free(Bm); free(gam); free(zet); free(b);
+      return 4;
+    }
+    if (indep) indep[i] = (uint8_t)res;
+    /* A^+ <- [A^+ - K b^T, K] */
+    for (int64_t c = 0; c < m; ++c) {
+      const double kc = st->K[c];
+      for (int64_t j = 0; j < i; ++j) {
+        if (mutation == 10) break;
+        Apinv[c * n + j] += (mutation == 11 ? kc * b[j] : -kc * b[j]);
+      }
+      Apinv[c * n + i] = kc;
+    }
+    /* B_{n+1} */
+    if (res == 1 && mutation != 12) {
+      for (int64_t k = 0; k < r_max; ++k) Bm[i * r_max + k] = 0.0;
+      Bm[i * r_max + r] = 1.0;
+    } else {
+      for (int64_t k = 0; k < r_max; ++k) Bm[i * r_max + k] = (k < r) ? gam[k] : 0.0;
+    }
+  }
+  if (rank_out) *rank_out = st->r;
+  rgo_release(st);
+  free(Bm); free(gam); free(zet); free(b);
+  return 0;
+}
+
+int rgo_pinv(int64_t n, int64_t m, const double *A, double tol, int test_mode, double *Apinv,
+             int64_t *rank_out, uint8_t *indep) {
+  return rgo_pinv_mut(n, m, A, tol, test_mode, 0, Apinv, rank_out, indep);
+}
+
+/*
  * Batched form: B independent streams in the packed layout (instance b: rows
  * A[elem_off[b] .. elem_off[b+1]) as n_b x m_b, targets Y[row_off[b] ..], solution
  * X[x_off[b] .. x_off[b] + m_b)). Instances run in parallel over `threads` OpenMP
