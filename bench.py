@@ -258,6 +258,32 @@ def run_gpu(args):
                 ms_k, r_k, _ = timed(mode, k, steps, 1)
                 extra[f"{mname}_k{k if k < n else 'all'}"] = {
                     "rows_per_s": n * steps / (ms_k / 1e3), "ms_per_step": ms_k / steps, "rank": r_k}
+    # --- pseudoinverse of the whole stream from its factorization (rg_pinv), FP64 and the
+    # orthonormal variant: 4 n m r flop per call
+    if not args.headline_only:
+        for flags, pname in ((rg.RG_FP64, "fp64"), (rg.RG_FP64 | rg.RG_ORTHONORMAL, "fp64_orthonormal")):
+            st = rg.RankGreville(M, 1e-10, flags)
+            st.add_rows(A, Y)
+            Ap = torch.empty((M, n), dtype=torch.float64, device=dev)
+            for _ in range(3):
+                st.pinv(A, Ap)
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            reps = 3
+            t0.record(stream)
+            for _ in range(reps):
+                st.pinv(A, Ap)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            ms_p = t0.elapsed_time(t1) / reps
+            rk = st.rank()
+            tflops = 4.0 * n * M * rk / (ms_p / 1e3) / 1e12
+            extra[f"pinv_{pname}_n{n}"] = {"ms_per_call": ms_p, "rank": rk, "tflops": tflops,
+                                          "frac_fp64_peak": tflops / fp64_peak_tflops(clocks.get("sm_mhz") or 2070.0)}
+            st.close()
+            del Ap
+            torch.cuda.empty_cache()
     # --- batched workloads
     if not args.headline_only and not args.quick:
         from paper_2106_11594_gb300 import inputs as _inp
@@ -463,11 +489,24 @@ def profile_case(name):
     """One untimed run of a small case of the hot path, for profilers (ncu -k/-c):
     stream-k32 / stream-kall (FP64 stream n=4096, m=1024, r=64 in 32-row calls / one
     call), stream-kall-mixed, batch-uniform-{mixed,fp64} (152 instances of n=2048, m=256,
-    r=32), batch-uneven-mixed (the first 512 shapes of the 4096-instance batch)."""
+    r=32), batch-uneven-mixed (the first 512 shapes of the 4096-instance batch), pinv
+    (rg_pinv of an FP64 stream n=16384, m=1024, r=64 after one call)."""
     import torch
 
     from paper_2106_11594_gb300 import inputs, rg
     dev = torch.device("cuda")
+    if name == "pinv":
+        s = inputs.large_stream(16384, M, R)
+        A = torch.from_numpy(s.A).to(dev)
+        Y = torch.from_numpy(s.Y).to(dev)
+        st = rg.RankGreville(M, 1e-10, rg.RG_FP64)
+        st.add_rows(A, Y)
+        Ap = torch.empty((M, s.n), dtype=torch.float64, device=dev)
+        st.pinv(A, Ap)
+        torch.cuda.synchronize()
+        print(name, "rank", st.rank())
+        st.close()
+        return
     if name.startswith("stream"):
         mode = rg.RG_MIXED if name.endswith("mixed") else rg.RG_FP64
         k = 32 if name == "stream-k32" else 4096
@@ -512,7 +551,7 @@ def main():
     ap.add_argument("--headline-only", action="store_true")
     ap.add_argument("--profile-case", default=None,
                     choices=["stream-k32", "stream-kall", "stream-kall-mixed", "batch-uniform-mixed",
-                             "batch-uniform-fp64", "batch-uneven-mixed"],
+                             "batch-uniform-fp64", "batch-uneven-mixed", "pinv"],
                     help="run one small untimed case for a profiler and exit")
     args = ap.parse_args()
     if args.profile_case:

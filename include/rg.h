@@ -137,6 +137,25 @@ rg_status rg_solution(rg_state* st, double* X, int64_t* rank_out);
 rg_status rg_adjoint(rg_state* st, const double* A, const double* y, int64_t n, const double* g,
                      double* gA, double* gy, double* X);
 
+/*
+ * rg_pinv -- the pseudoinverse A_n^+ (m x n) of the n rows the stream has taken since
+ * rg_init / rg_reset. Theorems label_th_pinv_indep and label_th_pinv_lindep update A^+ row
+ * by row (A^+ <- [A^+ - K b^T, K]); the library forms the same matrix after any call from
+ * the factorization it keeps, A^+ = D^T P^-1 B^T with B = A D^T (Section 2.1; D = Ct, or
+ * Q in the orthonormal variant), in 4 m n r FP64 flops.
+ *   A      device, n x m row-major: the rows fed, in order (the caller keeps them; the
+ *          result is only A^+ when they are exactly those rows).
+ *   n      number of rows fed, >= 0.
+ *   Apinv  device, m x n written with row stride ld: Apinv[c * ld + i] is entry (c, i) of
+ *          A^+ (coefficient c, observation i), so that X = A^+ y.
+ *   ld     row stride of Apinv, >= n.
+ * Reads the rank (synchronising), then runs asynchronously on the state's stream with a
+ * stream-ordered workspace of (m + n) r doubles. Ranks above 2048 give RG_EINVAL. A stream
+ * stopped by RG_ECAPACITY or RG_ENONFINITE still yields the pseudoinverse of the rows
+ * it applied (pass those rows).
+ */
+rg_status rg_pinv(rg_state* st, const double* A, int64_t n, double* Apinv, int64_t ld);
+
 /* rg_solution_host -- rg_solution into HOST memory X (m doubles). Synchronising. */
 rg_status rg_solution_host(rg_state* st, double* X, int64_t* rank_out);
 

@@ -396,6 +396,29 @@ rg_status rg_adjoint(rg_state* st, const double* A, const double* y, int64_t n, 
   return RG_OK;
 }
 
+rg_status rg_pinv(rg_state* st, const double* A, int64_t n, double* Apinv, int64_t ld) {
+  if (!valid_state(st)) return fail(RG_EINVAL, "rg_pinv: invalid state");
+  if (n < 0) return fail(RG_EINVAL, "rg_pinv: n = %lld < 0", (long long)n);
+  if (n > 0 && (!A || !Apinv)) return fail(RG_EINVAL, "rg_pinv: NULL buffer");
+  if (ld < n) return fail(RG_EINVAL, "rg_pinv: ld = %lld < n = %lld", (long long)ld, (long long)n);
+  int64_t r = 0;
+  rg_status s = rg_rank(st, &r);  // synchronises; a stream stopped by an error keeps a valid state
+  if (s != RG_OK && s != RG_ECAPACITY && s != RG_ENONFINITE) return s;
+  if (r > GRAM_RMAX) return fail(RG_EINVAL, "rg_pinv: rank %lld above %d", (long long)r, GRAM_RMAX);
+  if (n == 0) return RG_OK;
+  const size_t doubles = (size_t)std::max<long long>(1, ((long long)st->S.m + n) * r);
+  double* wk = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&wk, doubles * sizeof(double), st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_pinv: workspace");
+  e = launch_flush(flush_view(st), st->grid, st->stream);
+  if (e == cudaSuccess) e = launch_export_prep(st->S, st->grid, st->stream);  // P^-1 from P
+  if (e == cudaSuccess) e = launch_pinv(st->S, A, n, Apinv, ld, (int)r, wk, st->stream);
+  const cudaError_t e2 = cudaFreeAsync(wk, st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_pinv: launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "rg_pinv: workspace release");
+  return RG_OK;
+}
+
 rg_status rg_solution_host(rg_state* st, double* X, int64_t* rank_out) {
   if (!valid_state(st)) return fail(RG_EINVAL, "rg_solution_host: invalid state");
   if (!X) return fail(RG_EINVAL, "rg_solution_host: X is NULL");

@@ -23,6 +23,8 @@ cudaError_t launch_flush(const StreamDev& S, int grid, cudaStream_t stream);
 cudaError_t launch_solution(const StreamDev& S, double* X, cudaStream_t stream);
 cudaError_t launch_export(const StreamDev& S, double* C, double* Ct, double* Pinv, double* w,
                           long long* basis, cudaStream_t stream);
+cudaError_t launch_pinv(const StreamDev& S, const double* A, long long n, double* Apinv, long long ld,
+                        int r, double* wk, cudaStream_t stream);
 struct AdjArgs;
 cudaError_t launch_adjoint(const StreamDev& S, const AdjArgs& J, int grid, cudaStream_t stream);
 

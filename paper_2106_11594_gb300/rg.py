@@ -67,6 +67,7 @@ def lib(build: bool = True):
         "rg_batch_free": [vp],
         "rg_solve_noalloc": [vp, vp, i64, i64, f64, i32, i64, vp, vp, vp],
         "rg_adjoint": [vp, vp, vp, i64, vp, vp, vp, vp],
+        "rg_pinv": [vp, vp, i64, vp, i64],
         "rg_batch_adjoint": [vp, vp, vp, vp, vp, i64, vp, vp, vp, vp],
         "rg_batch_set_stream": [vp, vp],
         "rg_set_screen": [vp, f64],
@@ -159,6 +160,13 @@ class RankGreville:
         targets y fed since init/reset (float64 CUDA tensors)."""
         _check(lib().rg_adjoint(self._h, _ptr(A), _ptr(y), int(A.shape[0]), _ptr(g), _ptr(gA),
                                 _ptr(gy), _ptr(X)), "rg_adjoint")
+
+    def pinv(self, A, Apinv):
+        """rg_pinv: A^+ (m x n) of the rows A (n x m) fed since init/reset into Apinv, a
+        float64 CUDA tensor of shape (m, ld >= n) (row stride ld)."""
+        assert Apinv.dim() == 2 and Apinv.shape[0] == self.m and Apinv.stride(1) == 1
+        _check(lib().rg_pinv(self._h, _ptr(A), int(A.shape[0]), _ptr(Apinv), int(Apinv.stride(0))),
+               "rg_pinv")
 
     def set_screen(self, tau_lo: float):
         """rg_set_screen: floor of mixed mode's FP32 screen."""
