@@ -175,8 +175,10 @@ def run_gpu(args):
         st.reset()
         for c, j0 in enumerate(range(0, n, k)):
             # launch durations are sampled on every 16th call: an event pair around every
-            # launch would itself slow the timed region by ~15 %
-            sample = ev is not None and c % 16 == 0
+            # launch would itself slow the timed region by ~15 %. The sample starts at call
+            # 15, past the two rank-growth calls (0, 1) whose section scan makes them ~20x
+            # longer: counted once per 16 calls they would weigh 8x their share of the step
+            sample = ev is not None and c % 16 == 15
             if sample:
                 ev[0].append(torch.cuda.Event(enable_timing=True))
                 ev[0][-1].record(stream)
