@@ -894,26 +894,45 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
       return d;
     };
     if constexpr (kGrid) {
+      static_assert(4 * NWARP == SLOW_MAX, "four section rows per warp");
       if (reg) {
+      // Each CTA owns 32 columns (lane = column); warp w holds the rejections of section
+      // rows 4w .. 4w + 3 on them, so the FP64 work of a row (its products with the later
+      // rows and their fix-ups) is spread over the 8 warps and the SM's four FP64 units.
       const int lane = tid & 31, warp = tid >> 5;
       const long long c = (long long)T.id() * 32 + lane;
-      const bool cv = warp == 0 && c < m;
-      double R[32];
+      const bool colv = c < m;
+      __shared__ double rcur[32];   // the current row's rejection on the CTA's columns
+      __shared__ double cpart[32];  // the CTA's part of R_jj . R_t for section rows t
+      double Rw[4];
 #pragma unroll
-      for (int k = 0; k < 32; ++k) R[k] = (cv && k < nrow) ? __ldcg(S.R + (size_t)k * ld + c) : 0.0;
+      for (int i = 0; i < 4; ++i) {
+        const int t = 4 * warp + i;
+        Rw[i] = (colv && t < nrow) ? __ldcg(S.R + (size_t)t * ld + c) : 0.0;
+      }
       for (int jj = 0; jj < nrow; ++jj) {
-        if (warp == 0) {
-          double v[32];
+        if (warp == (jj >> 2)) {
+          const int i = jj & 3;
+          rcur[lane] = i == 0 ? Rw[0] : i == 1 ? Rw[1] : i == 2 ? Rw[2] : Rw[3];
+        }
+        __syncthreads();
+        const double rj = rcur[lane];
+        double v[4];
 #pragma unroll
-          for (int k = 0; k < 32; ++k) v[k] = R[0] * R[k];
-          warp_transpose_sum32(v);  // lane k: this CTA's part of value k
-          if (nact > 1) S.Sp[(size_t)(jj & 1) * S.sp_stride + (size_t)T.id() * 32 + lane] = v[0];
-          else tot[lane] = v[0];
+        for (int i = 0; i < 4; ++i) v[i] = (4 * warp + i >= jj) ? rj * Rw[i] : 0.0;
+        warp_transpose_sum<double, 4>(v);
+        if ((lane & 7) == 0) cpart[4 * warp + transpose_sum_index<4>()] = v[0];
+        __syncthreads();
+        if (tid < 32) {  // lane k: row jj + k
+          const double pv = (jj + tid < 32) ? cpart[jj + tid] : 0.0;
+          if (nact > 1) S.Sp[(size_t)(jj & 1) * S.sp_stride + (size_t)T.id() * 32 + tid] = pv;
+          else tot[tid] = pv;
         }
         if (nact > 1) {
           if (!sub_barrier(S.ctrl, nact, bar_target)) return false;
-          // value k = lane, summed over the owners w = warp, warp + NWARP, ... then over warps
-          // (all loads issued before the adds: up to 20 owners per warp)
+          // value k = lane, summed over the owners w = warp, warp + NWARP, ... (a fixed
+          // pairwise tree, all loads issued first: up to 20 owners per warp), then over
+          // the warps; every CTA sums in the same order
           const double* Sp = S.Sp + (size_t)(jj & 1) * S.sp_stride;
           double pv[20];
 #pragma unroll
@@ -921,16 +940,17 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
             const int w2 = warp + q * NWARP;
             pv[q] = (w2 < nact) ? __ldcg(Sp + (size_t)w2 * 32 + lane) : 0.0;
           }
-          double a = 0.0;
 #pragma unroll
-          for (int q = 0; q < 20; ++q) a += pv[q];
-          wred[warp][lane] = a;
+          for (int h = 16; h >= 1; h >>= 1)
+#pragma unroll
+            for (int q = 0; q < h; ++q)
+              if (q + h < 20) pv[q] += pv[q + h];
+          wred[warp][lane] = pv[0];
           __syncthreads();
           if (tid < 32) {
-            double t2 = 0.0;
-#pragma unroll
-            for (int w2 = 0; w2 < NWARP; ++w2) t2 += wred[w2][tid];
-            tot[tid] = t2;
+            const double a0 = wred[0][tid] + wred[1][tid], a1 = wred[2][tid] + wred[3][tid];
+            const double a2 = wred[4][tid] + wred[5][tid], a3 = wred[6][tid] + wred[7][tid];
+            tot[tid] = (a0 + a1) + (a2 + a3);
           }
         }
         __syncthreads();
@@ -942,15 +962,15 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
         if (d == 1) {
           const double is = is_s;
           const double scale = ORTHO ? rsq_s : is;
-          if (cv) S.Kv[(size_t)nind * ld + c] = R[0] * scale;
+          if (warp == 0 && colv) S.Kv[(size_t)nind * ld + c] = rj * scale;
 #pragma unroll
-          for (int k = 1; k < 32; ++k) R[k] = fma(-tot[k] * is, R[0], R[k]);
+          for (int i = 0; i < 4; ++i) {
+            const int t = 4 * warp + i;
+            if (t > jj) Rw[i] = fma(-tot[t - jj] * is, rj, Rw[i]);
+          }
           ++rc;
           ++nind;
         }
-#pragma unroll
-        for (int k = 0; k < 31; ++k) R[k] = R[k + 1];
-        R[31] = 0.0;
       }
       }
     }
