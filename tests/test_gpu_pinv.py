@@ -127,3 +127,29 @@ def test_pinv_full_size_single_stream():
     u = torch.from_numpy(inputs.rng_for(303, 0).standard_normal(n)).to(dev)
     v = Ap @ u
     assert checks.rel_err((Ap @ (At @ v)).cpu().numpy(), v.cpu().numpy()) <= tol_pinv
+
+
+def test_pinv_after_capacity_stop_and_argument_checks():
+    """A stream stopped by RG_ECAPACITY keeps the rows it applied: rg_pinv of those rows
+    is their pseudoinverse. Bad arguments are refused on the host."""
+    torch, dev = torch_cuda()
+    s = inputs.large_stream(200, 40, 12)
+    At = torch.from_numpy(s.A).to(dev)
+    Yt = torch.from_numpy(s.Y).to(dev)
+    st = rg.RankGreville(40, 1e-10, rg.RG_FP64, rg.RG_TEST_REL, 8)  # r_max 8 < rank 12
+    st.add_rows(At, Yt)
+    X = torch.empty(40, dtype=torch.float64, device=dev)
+    with pytest.raises(rg.RGError) as ei:
+        st.solution(X)
+    assert ei.value.code == rg.RG_ECAPACITY
+    n_ok = st.rows_seen()
+    assert n_ok == 8  # the first 12 rows are independent; the ninth stops the stream
+    Ap = torch.empty((40, n_ok), dtype=torch.float64, device=dev)
+    st.pinv(At[:n_ok], Ap)
+    ref, _, _ = fp64.pinv(s.A[:n_ok], 1e-10)
+    assert checks.rel_err(Ap.cpu().numpy(), ref) <= TOL64
+    Ap2 = torch.empty((40, 4), dtype=torch.float64, device=dev)
+    with pytest.raises(rg.RGError) as ei:
+        st.pinv(At[:n_ok], Ap2)  # row stride 4 < n
+    assert ei.value.code == rg.RG_EINVAL
+    st.close()
