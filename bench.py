@@ -260,6 +260,10 @@ def run_gpu(args):
                 ms_k, r_k, _ = timed(mode, k, steps, 1)
                 extra[f"{mname}_k{k if k < n else 'all'}"] = {
                     "rows_per_s": n * steps / (ms_k / 1e3), "ms_per_step": ms_k / steps, "rank": r_k}
+        for k in (32, n):  # the FP64 orthonormal variant (Section 2.2)
+            ms_k, r_k, _ = timed(rg.RG_FP64 | rg.RG_ORTHONORMAL, k, 2, 1)
+            extra[f"fp64_orthonormal_k{k if k < n else 'all'}"] = {
+                "rows_per_s": n * 2 / (ms_k / 1e3), "ms_per_step": ms_k / 2, "rank": r_k}
     # --- pseudoinverse of the whole stream from its factorization (rg_pinv), FP64 and the
     # orthonormal variant: 4 n m r flop per call
     if not args.headline_only:
@@ -297,6 +301,9 @@ def run_gpu(args):
             extra[f"batch_uniform1024_{mname}"] = run_batched("uniform", shapes4, 4, 1e-3, mode, 2, 1, dev, ws, rank)
             extra[f"adjoint_uniform1024_{mname}"] = run_batched("uniform", shapes4, 4, 1e-3, mode, 2, 1, dev, ws, rank,
                                                                backward=True)
+        # the orthonormal variant of Section 2.2 with every step in FP64
+        extra["batch_uniform1024_fp64_orthonormal"] = run_batched(
+            "uniform", shapes4, 4, 1e-3, rg.RG_FP64 | rg.RG_ORTHONORMAL, 2, 1, dev, ws, rank)
     # --- roofline of the dominant kernel (the stream kernel, one launch per 32-row call)
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak = fp64_peak_tflops(sm_mhz)

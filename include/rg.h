@@ -63,8 +63,8 @@ enum {
   RG_ORTHONORMAL = 4  /* keep the orthonormal variant of Section 2.2 (alpha_{n+1} =
                          1/||Gamma_r||: the basis rows are orthonormal and serve as their
                          own dual basis) instead of Algorithm 1's raw rows and dual basis.
-                         RG_MIXED always uses it; with RG_FP64 it is opt-in (rg_init and
-                         rg_solve_noalloc; not rg_batch_init)                        */
+                         RG_MIXED always uses it; with RG_FP64 it is opt-in (rg_init,
+                         rg_solve_noalloc and rg_batch_init)                         */
 };
 
 /*

@@ -23,7 +23,7 @@
 namespace rg {
 
 struct BatchDev {
-  int B, mixed, test_mode, kb_max, ld_max, r_max_max, nmc_max;
+  int B, mixed, ortho, test_mode, kb_max, ld_max, r_max_max, nmc_max;
   int kb_cap;  // rows of block scratch laid out per CTA (kb_max <= kb_cap)
   double tol, tau_lo;
   const int* m;               // B
@@ -43,7 +43,7 @@ struct BatchDev {
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Instance state layout; fills S's state pointers when base != null. Returns bytes.
-__host__ __device__ inline size_t inst_layout(int m, int ld, int rmax, int mixed, char* base,
+__host__ __device__ inline size_t inst_layout(int m, int ld, int rmax, int mixed, int ortho, char* base,
                                               StreamDev* S) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -52,7 +52,7 @@ __host__ __device__ inline size_t inst_layout(int m, int ld, int rmax, int mixed
     return p;
   };
   char* C = take((size_t)rmax * ld * 8);
-  char* Ct = mixed ? nullptr : take((size_t)rmax * ld * 8);
+  char* Ct = ortho ? nullptr : take((size_t)rmax * ld * 8);
   char* Qf = mixed ? take((size_t)rmax * ld * 4) : nullptr;
   char* P = take((size_t)rmax * rmax * 8);
   char* wb = take((size_t)rmax * 8);
@@ -131,7 +131,7 @@ __host__ __device__ inline size_t scratch_layout(int kb, int ldm, int rmm, int n
 // CTA's tensor-core context: one mbarrier and TC_TMEM_COLS columns of tensor memory (one
 // CTA per SM in mixed mode, so the 512 columns of an SM always suffice). FP64 mode runs two
 // CTAs per SM; mixed mode one, with the register budget that its staging needs.
-template <bool MIXED>
+template <bool MIXED, bool ORTHO>
 __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, const double* __restrict__ Gp,
                                                    const int64_t* __restrict__ roff,
                                                    const int64_t* __restrict__ eoff,
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, co
   S.Rs = reinterpret_cast<double*>(dyn_base);
   S.rs_cap = ((MIXED ? TC_SMEM_MIXED : TC_SMEM) - 1024) / 8;
   S.mixed = MIXED;
-  S.ortho = MIXED;
+  S.ortho = ORTHO;
   S.test_mode = D.test_mode;
   S.tol = D.tol;
   S.tau_lo = D.tau_lo;
@@ -202,11 +202,11 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, co
     S.ld = (m + 3) / 4 * 4;
     S.r_max = D.r_max[b];
     S.nmc = (m + MC - 1) / MC;
-    inst_layout(m, S.ld, S.r_max, MIXED, D.state + D.soff[b], &S);
+    inst_layout(m, S.ld, S.r_max, MIXED, ORTHO, D.state + D.soff[b], &S);
     S.ctrl = D.ctrl + (size_t)b * CTRL_N;
     S.rows_seen = D.rows_seen + b;
     CallArgs A{Gp + eoff[b], yp + roff[b], n, indep ? indep + roff[b] : nullptr};
-    const bool ok = process_rows<CtaTeam, MIXED>(CtaTeam{}, S, A);
+    const bool ok = process_rows<CtaTeam, MIXED, ORTHO>(CtaTeam{}, S, A);
     __syncthreads();
     if (threadIdx.x == 0) {
       const int st = ld_acquire_i32(S.ctrl + CTRL_STATUS);
@@ -221,6 +221,12 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, co
     if (threadIdx.x < 32)
       asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tcx.tmem), "r"(TC_TMEM_COLS));
   }
+}
+
+// FP32 projections always come with the orthonormal variant.
+static const void* batch_kernel_ptr(int mixed, int ortho) {
+  if (mixed) return (const void*)batch_kernel<true, true>;
+  return ortho ? (const void*)batch_kernel<false, true> : (const void*)batch_kernel<false, false>;
 }
 
 // Longest-first order of the instances for this call (single CTA, bitonic sort in shared
@@ -282,11 +288,11 @@ __global__ void __launch_bounds__(NT, 2) batch_solution_kernel(BatchDev D, doubl
     S.ld = ld;
     S.r_max = D.r_max[b];
     S.ctrl = D.ctrl + (size_t)b * CTRL_N;
-    inst_layout(m, ld, D.r_max[b], D.mixed, D.state + D.soff[b], &S);
+    inst_layout(m, ld, D.r_max[b], D.mixed, D.ortho, D.state + D.soff[b], &S);
     const int r = D.ctrl[(size_t)b * CTRL_N + CTRL_R];
     __syncthreads();
     form_w(S, r);
-    const double* Bm = D.mixed ? S.C : S.Ct;
+    const double* Bm = D.ortho ? S.C : S.Ct;
     const long long x0 = xoff ? xoff[b] : D.xoff_def[b];
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
       double acc = 0.0;
@@ -328,9 +334,9 @@ __global__ void __launch_bounds__(NT, 2) batch_adjoint_kernel(BatchDev D, const 
     S.ld = (m + 3) / 4 * 4;
     S.r_max = D.r_max[b];
     S.mixed = D.mixed;
-    S.ortho = D.mixed;
+    S.ortho = D.ortho;
     S.ctrl = D.ctrl + (size_t)b * CTRL_N;
-    inst_layout(m, S.ld, S.r_max, D.mixed, D.state + D.soff[b], &S);
+    inst_layout(m, S.ld, S.r_max, D.mixed, D.ortho, D.state + D.soff[b], &S);
     const int r = D.ctrl[(size_t)b * CTRL_N + CTRL_R];
     __syncthreads();
     form_w(S, r);
@@ -409,8 +415,6 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
   if (!m) return fail(RG_EINVAL, "rg_batch_init: m is NULL");
   if (std::isnan(tol)) return fail(RG_EINVAL, "rg_batch_init: tol is NaN");
   if (flags & ~(RG_MIXED | RG_TEST_PAPER | RG_ORTHONORMAL)) return fail(RG_EINVAL, "rg_batch_init: unknown flags %d", flags);
-  if ((flags & RG_ORTHONORMAL) && !(flags & RG_MIXED))
-    return fail(RG_EINVAL, "rg_batch_init: the FP64 orthonormal variant is available for single streams only");
   rg_batch* bt = new (std::nothrow) rg_batch();
   if (!bt) return fail(RG_ENOMEM, "rg_batch_init: host allocation failed");
   bt->m.resize(B);
@@ -437,6 +441,7 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
   BatchDev& D = bt->D;
   D.B = (int)B;
   D.mixed = (flags & RG_MIXED) ? 1 : 0;
+  D.ortho = (flags & (RG_MIXED | RG_ORTHONORMAL)) ? 1 : 0;
   D.test_mode = (flags & RG_TEST_PAPER) ? 2 : 0;
   D.tol = tol;
   D.tau_lo = 1e-5;
@@ -450,15 +455,11 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
   int nsm = 0, per = 0;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, bt->device);
   const int dyn = D.mixed ? TC_SMEM_MIXED : TC_SMEM;
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(D.mixed ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  const void* kfn = batch_kernel_ptr(D.mixed, D.ortho);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
   if (e == cudaSuccess)  // up to two CTAs of ~105 KiB each per SM
-    e = cudaFuncSetAttribute(D.mixed ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per, D.mixed ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>, NT, dyn);
+    e = cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, NT, dyn);
   if (e != cudaSuccess || per <= 0) {
     delete bt;
     return e != cudaSuccess ? cuda_fail(e, "rg_batch_init: occupancy") : fail(RG_ECUDA, "rg_batch_init: no occupancy");
@@ -471,7 +472,7 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
   for (int64_t b = 0; b < B; ++b) {
     soff[b] = (long long)state_bytes;
     const int ld = (bt->m[b] + 3) / 4 * 4;
-    state_bytes += inst_layout(bt->m[b], ld, bt->r_max[b], D.mixed, nullptr, nullptr);
+    state_bytes += inst_layout(bt->m[b], ld, bt->r_max[b], D.mixed, D.ortho, nullptr, nullptr);
     xoff[b + 1] = xoff[b] + bt->m[b];
   }
   StreamDev tmp{};
@@ -541,11 +542,14 @@ rg_status rg_batch_add_rows(rg_batch* bt, const double* Gamma_packed, const int6
     // kernel writes every applied row and the rest are left as the caller initialised them
   }
   if (D.mixed)
-    batch_kernel<true><<<bt->grid, NT, TC_SMEM_MIXED, bt->stream>>>(D, Gamma_packed, row_offsets, elem_offsets,
-                                                        y_packed, indep_out);
+    batch_kernel<true, true><<<bt->grid, NT, TC_SMEM_MIXED, bt->stream>>>(D, Gamma_packed, row_offsets,
+                                                                   elem_offsets, y_packed, indep_out);
+  else if (D.ortho)
+    batch_kernel<false, true><<<bt->grid, NT, TC_SMEM, bt->stream>>>(D, Gamma_packed, row_offsets,
+                                                               elem_offsets, y_packed, indep_out);
   else
-    batch_kernel<false><<<bt->grid, NT, TC_SMEM, bt->stream>>>(D, Gamma_packed, row_offsets, elem_offsets,
-                                                         y_packed, indep_out);
+    batch_kernel<false, false><<<bt->grid, NT, TC_SMEM, bt->stream>>>(D, Gamma_packed, row_offsets,
+                                                                elem_offsets, y_packed, indep_out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "rg_batch_add_rows: launch");
   return RG_OK;

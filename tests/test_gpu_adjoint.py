@@ -106,7 +106,8 @@ def test_gradcheck_full_rank():
     assert torch.autograd.gradcheck(lambda a, b: lstsq_rg(a, b), (A, y), eps=1e-6, atol=1e-8, rtol=1e-6)
 
 
-@pytest.mark.parametrize("mode,tol", [(rg.RG_FP64, 1e-9), (rg.RG_MIXED, 1e-3)])
+@pytest.mark.parametrize("mode,tol", [(rg.RG_FP64, 1e-9), (rg.RG_FP64 | rg.RG_ORTHONORMAL, 1e-9),
+                                      (rg.RG_MIXED, 1e-3)])
 def test_batch_adjoint_matches_oracle(mode, tol):
     torch, dev = torch_cuda()
     from paper_2106_11594_gb300.autograd import lstsq_rg_batch

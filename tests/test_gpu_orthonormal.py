@@ -8,7 +8,7 @@ by 1e3, as for the general variant."""
 import numpy as np
 import pytest
 
-from gpu_helpers import run_stream, torch_cuda
+from gpu_helpers import run_batch, run_stream, torch_cuda
 from oracle import checks, fp64
 from paper_2106_11594_gb300 import inputs, rg
 
@@ -99,6 +99,21 @@ def test_noalloc_fp64_orthonormal():
     assert checks.rel_err(X.cpu().numpy(), o.X) <= TOL64
 
 
-def test_batch_rejects_fp64_orthonormal():
-    with pytest.raises(rg.RGError):
-        rg.RankGrevilleBatch([32, 48], 1e-10, ORTHO64)
+@pytest.mark.parametrize("calls", [1, 2])
+def test_batch_fp64_orthonormal(calls):
+    """The batched kernel's FP64 orthonormal instantiation against the oracle's orthonormal
+    variant, instance by instance (32 instances spread over the uneven batch). The bar of
+    an ill-conditioned instance is max(1e-10, 1e3 eps kappa_2(A)), as for the general
+    variant."""
+    batch = inputs.uneven_batch(4096, instances=list(range(0, 4096, 128)))
+    ores = [fp64.solve(s.A, s.Y, tol=1e-10, variant=fp64.ORTHONORMAL) for s in batch.streams]
+    g = run_batch(batch, mode=ORTHO64, calls=calls)
+    for b, (s, o) in enumerate(zip(batch.streams, ores)):
+        assert g["ranks"][b] == o.rank, b
+        rb = int(g["row_base"][b])
+        np.testing.assert_array_equal(g["indep"][rb:rb + s.n], o.indep, err_msg=f"instance {b}")
+        X = g["X"][g["xo"][b]:g["xo"][b + 1]]
+        sv = np.linalg.svd(s.A, compute_uv=False)
+        sv = sv[sv > sv[0] * 1e-12]
+        tb = max(TOL64, 1e3 * np.finfo(float).eps * sv[0] / sv[-1])
+        assert checks.rel_err(X, o.X) <= tb, (b, checks.rel_err(X, o.X), tb)
