@@ -437,3 +437,20 @@ def test_orthonormal_planted_mistakes_fail_a_pin(mutation):
     Xs = np.linalg.lstsq(A, Y, rcond=None)[0]
     assert checks.rel_err(o.X, Xs) > 1e-6 or np.abs(
         o.Pinv @ ((A @ o.C.T).T @ (A @ o.C.T)) - np.eye(o.rank)).max() > 1e-6
+
+
+def test_ill_conditioned_generator_growth_and_the_method_noise_floor():
+    """The ill-conditioned generator's rank-growth trajectory is the prefix rank (checked
+    by SVD at every prefix of a mildly conditioned case, s in [0.1, 1]). Both variants of
+    the method follow it at tol 1e-9 and 1e-8. At tol 1e-10 they do not: one classical
+    Gram-Schmidt pass leaves a dependent row's relative rejection near 1e-10 after the
+    last direction of a phase is appended with a relative rejection of 6e-3, so rows past
+    it are declared independent (Section 4.2: the method is not forward stable)."""
+    s = inputs.ill_conditioned_stream(n=512, m=96, r=16, s_lo=1e-1)
+    prefix = [np.linalg.matrix_rank(s.A[:i + 1]) for i in range(s.n)]
+    np.testing.assert_array_equal(np.diff([0] + prefix), s.growth)
+    for variant in (fp64.GENERAL, fp64.ORTHONORMAL):
+        for tol in (1e-9, 1e-8):
+            o = fp64.solve(s.A, s.Y, tol=tol, variant=variant)
+            np.testing.assert_array_equal(o.indep, s.growth)
+        assert fp64.solve(s.A, s.Y, tol=1e-10, variant=variant).rank > s.rank
