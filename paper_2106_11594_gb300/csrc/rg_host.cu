@@ -287,16 +287,21 @@ rg_status rg_add_rows_host(rg_state* st, const double* Gamma, const double* y, i
   if (k == 0) return RG_OK;
   if (!Gamma || !y) return fail(RG_EINVAL, "rg_add_rows_host: NULL rows or targets");
   const long long m = st->S.m;
-  if (!st->stage) {
+  if (st->stage_rows == 0) {  // first use: all of the staging resources, or none
     long long rows = std::max<long long>(1, (32ll << 20) / (8 * (m + 1)));
-    cudaError_t e = cudaMalloc(&st->stage, 2 * (size_t)rows * (size_t)(m + 1) * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&st->stage_ind, (size_t)rows);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st->copy_stream, cudaStreamNonBlocking);
+    cudaError_t e = cudaSuccess;
+    if (!st->stage) e = cudaMalloc(&st->stage, 2 * (size_t)rows * (size_t)(m + 1) * 8);
+    if (e == cudaSuccess && !st->stage_ind) e = cudaMalloc(&st->stage_ind, (size_t)rows);
+    if (e == cudaSuccess && !st->copy_stream)
+      e = cudaStreamCreateWithFlags(&st->copy_stream, cudaStreamNonBlocking);
     for (int h = 0; h < 2 && e == cudaSuccess; ++h) {
-      e = cudaEventCreateWithFlags(&st->copied[h], cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->consumed[h], cudaEventDisableTiming);
+      if (!st->copied[h]) e = cudaEventCreateWithFlags(&st->copied[h], cudaEventDisableTiming);
+      if (e == cudaSuccess && !st->consumed[h])
+        e = cudaEventCreateWithFlags(&st->consumed[h], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventRecord(st->consumed[h], st->stream);
     }
+    // on failure what was created stays owned by the state (rg_free releases it) and the
+    // next call retries the rest
     if (e != cudaSuccess) return cuda_fail(e, "rg_add_rows_host: staging allocation");
     st->stage_rows = rows;
   }
