@@ -38,9 +38,9 @@ METRIC = ("row updates/sec (device-timed, batched & single) at stated rel. error
 WORKLOAD = f"single FP64 stream n={N_ROWS} m={M} r={R}, k={K_CALL} rows per rg_add_rows call"
 
 
-# DRAM bytes (read + write) of one 32-row stream_kernel<false, false> launch, from the ncu capture
-# summarised in profiles/stream_kernel_fp64_k32_n4096_full.md, and the hash of the kernel
-# sources it was taken on: once the sources change the figure no longer applies (null).
+# DRAM bytes (read + write) of one 32-row stream_kernel<false, false> launch, from the ncu
+# capture of that kernel summarised under profiles/, and the hash of the kernel sources it
+# was taken on: once the sources change the figure no longer applies (null).
 TRAFFIC_BYTES_PER_LAUNCH = 1465600
 TRAFFIC_SOURCES_SHA = "5083b1f17f1c9ba7"
 
