@@ -79,13 +79,15 @@ class Result:
     status: int
 
 
-GENERAL, ORTHONORMAL = 0, 1
+GENERAL, ORTHONORMAL, ORTHOGONAL = 0, 1, 2
 
 
 def solve(A, Y, tol: float = 1e-10, test_mode: int = TEST_REL, r_max: int = 0,
           mutation: int = 0, variant: int = GENERAL) -> Result:
     """Run Algorithm 1 over all rows of A (n x m) with targets Y, from an empty state.
-    variant=ORTHONORMAL takes Section 2.2's orthonormal rank factorization (C = Ct = Q)."""
+    variant=ORTHONORMAL takes Section 2.2's orthonormal rank factorization (C = Ct = Q);
+    variant=ORTHOGONAL its orthogonal one (alpha = 1: C holds the raw rejections, Ct the
+    same rows divided by their squared norms)."""
     A = np.ascontiguousarray(A, dtype=np.float64)
     Y = np.ascontiguousarray(Y, dtype=np.float64).reshape(-1)
     n, m = A.shape

@@ -28,7 +28,9 @@
  *       P^-1 = [[P^-1, -alpha zeta], [-alpha zeta^T, alpha^2 (1 + gamma^T zeta)]],
  *              zeta = P^-1 gamma
  * (so the rows of C are orthonormal and Ct = C); K, the dependent case and the X update
- * are unchanged, since Theorems 4 and 5 hold for any rank factorization.
+ * are unchanged, since Theorems 4 and 5 hold for any rank factorization. The orthogonal
+ * variant of the same section takes alpha = 1: C stores the raw rejections (orthogonal,
+ * not normalised) and Ct the same rows divided by their squared norms.
  *
  * Readings of the paper taken here (each listed in the design notes):
  *  - Threshold (Eq. label_eq_eps). Two modes. REL (default): independent iff
@@ -63,7 +65,7 @@ typedef struct {
   double tol;
   int test_mode;
   int mutation;
-  int variant;  /* 0: general (Algorithm 1), 1: orthonormal (Section 2.2) */
+  int variant;  /* 0: general (Algorithm 1), 1: orthonormal, 2: orthogonal (Section 2.2) */
   double *C;    /* r_max x m, row i = i-th basis row (a selected input row)      */
   double *Ct;   /* r_max x m, row i = i-th dual basis row                          */
   double *Pinv; /* r_max x r_max, leading r x r block is P^-1 = (B^T B)^-1         */
@@ -139,9 +141,10 @@ static int rgo_update(rgo_state *st, const double *G, double y) {
     t += G[c] * G[c];
   }
   int indep = rgo_is_independent(st, s, t);
-  if (indep && st->variant == 1) {
+  if (indep && (st->variant == 1 || st->variant == 2)) {
     if (r >= st->r_max) return -4;
-    const double alpha = 1.0 / sqrt(s);
+    /* orthonormal: alpha = 1 / ||Gamma_r||; orthogonal: alpha = 1 (the raw rejection) */
+    const double alpha = (st->variant == 2) ? 1.0 : 1.0 / sqrt(s);
     /* zeta <- P^-1 gamma (for the bordered P^-1) */
     for (int64_t i = 0; i < r; ++i) {
       double acc = 0.0;

@@ -395,48 +395,74 @@ def test_orthonormal_and_general_agree_and_follow_the_prefix_rank():
     assert checks.rel_err(o.X, g.X) < 1e-11
 
 
-def test_golden_orthonormal_variant_metrics():
-    """The orthonormal columns of Tables table_e_Pascal / table_res_Pascal,
-    table_e_USV / table_res_USV and table_res_Kahan: the orthonormal oracle lands within
+@pytest.mark.parametrize("variant,col", [(fp64.ORTHONORMAL, "orthonormal"), (fp64.ORTHOGONAL, "orthogonal")])
+def test_golden_section_2_2_variant_metrics(variant, col):
+    """The orthonormal and orthogonal columns of Tables table_e_Pascal / table_res_Pascal,
+    table_e_USV / table_res_USV and table_res_Kahan: each variant of the oracle lands within
     the same factors as the general one (30 for Pascal and the USV medians, 3 for Kahan).
-    A printed residual within 100 machine epsilons of zero (P(4): 1.83e-15) is rounding
-    noise whose size depends on the operation order, so there only the upper bound holds."""
+    A printed residual within 100 machine epsilons of zero (P(4): 1.83e-15 and 5.99e-16)
+    is rounding noise whose size depends on the operation order, so there only the upper
+    bound holds."""
     eps_m = GOLDEN["machine_epsilon"]["eps_M"]
     g = GOLDEN["pascal"]
-    for n, e_ref, r_ref in zip(g["n"], g["e_orthonormal"], g["res_orthonormal"]):
+    for n, e_ref, r_ref in zip(g["n"], g["e_" + col], g["res_" + col]):
         A = inputs.pascal(n)
         Linv = np.array([[(-1) ** (i - j) * comb(i, j) for j in range(n)] for i in range(n)], float)
-        Ap = pinv_by_unit_targets(A, 1e-30, fp64.ORTHONORMAL)
+        Ap = pinv_by_unit_targets(A, 1e-30, variant)
         e = checks.stability_factor(Ap, Linv.T @ Linv, A)
         res = checks.residual_error(Ap, A)
         assert e_ref / 30 <= e <= e_ref * 30, (n, e, e_ref)
         lo = r_ref / 30 if r_ref > 100 * eps_m else 0.0
         assert lo <= res <= r_ref * 30, (n, res, r_ref)
     g = GOLDEN["usv"]
-    for n, e_ref, r_ref in zip(g["n"], g["e_orthonormal"], g["res_orthonormal"]):
+    for n, e_ref, r_ref in zip(g["n"], g["e_" + col], g["res_" + col]):
         es, rs = [], []
         for seed in range(5):
             A, U, S, V = inputs.usv(n, seed)
-            Ap = pinv_by_unit_targets(A, g["eps"], fp64.ORTHONORMAL)
+            Ap = pinv_by_unit_targets(A, g["eps"], variant)
             ref = V @ np.diag(1 / np.diag(S)) @ U.T
             es.append(checks.stability_factor(Ap, ref, A))
             rs.append(checks.residual_error(Ap, A))
         assert e_ref / 30 <= np.median(es) <= e_ref * 30, (n, es, e_ref)
         assert r_ref / 30 <= np.median(rs) <= r_ref * 30, (n, rs, r_ref)
     g = GOLDEN["kahan"]
-    for c, ref in zip(g["c"], g["res_orthonormal"]):
+    for c, ref in zip(g["c"], g["res_" + col]):
         A = inputs.kahan(g["n"], c)
-        res = checks.residual_error(pinv_by_unit_targets(A, 1e-30, fp64.ORTHONORMAL), A)
+        res = checks.residual_error(pinv_by_unit_targets(A, 1e-30, variant), A)
         assert ref / 3 <= res <= ref * 3, (c, res, ref)
 
 
-@pytest.mark.parametrize("mutation", [8, 9])
-def test_orthonormal_planted_mistakes_fail_a_pin(mutation):
+def test_orthogonal_variant_basis_and_solution():
+    """alpha = 1 (Section 2.2): the basis rows are the raw rejections, mutually orthogonal;
+    the dual basis is the same rows divided by their squared norms; P^-1 = (B^T B)^-1 with
+    B = A Ct^T; the solution is the SVD least-squares one and equals the other variants'."""
+    A, Y = _rank_deficient(50, 16, 6, 8)
+    o = fp64.solve(A, Y, tol=1e-10, variant=fp64.ORTHOGONAL)
+    C, Ct = o.C, o.Ct
+    G = C @ C.T
+    assert np.abs(G - np.diag(np.diag(G))).max() < 1e-12 * np.abs(G).max()  # orthogonal rows
+    assert np.abs(Ct - C / np.diag(G)[:, None]).max() < 1e-13 * np.abs(Ct).max()
+    B = A @ Ct.T
+    assert np.abs(o.Pinv @ (B.T @ B) - np.eye(o.rank)).max() < 1e-10
+    assert checks.rel_err(o.X, np.linalg.lstsq(A, Y, rcond=None)[0]) < 1e-11
+    assert checks.rel_err(o.X, fp64.solve(A, Y, tol=1e-10, variant=fp64.ORTHONORMAL).X) < 1e-12
+    assert checks.rel_err(o.X, fp64.solve(A, Y, tol=1e-10).X) < 1e-11
+
+
+@pytest.mark.parametrize("variant,mutation", [(fp64.ORTHONORMAL, 8), (fp64.ORTHONORMAL, 9),
+                                               (fp64.ORTHOGONAL, 9)])
+def test_section_2_2_planted_mistakes_fail_a_pin(variant, mutation):
+    """alpha^2 dropped from the border (invisible at alpha = 1, so orthonormal only) and the
+    border's sign flipped."""
     A, Y = _rank_deficient(40, 12, 5, 6)
-    o = fp64.solve(A, Y, tol=1e-10, variant=fp64.ORTHONORMAL, mutation=mutation)
     Xs = np.linalg.lstsq(A, Y, rcond=None)[0]
-    assert checks.rel_err(o.X, Xs) > 1e-6 or np.abs(
-        o.Pinv @ ((A @ o.C.T).T @ (A @ o.C.T)) - np.eye(o.rank)).max() > 1e-6
+
+    def pins_fail(o):
+        B = A @ o.Ct.T  # B = A Ct^T for any of the factorizations
+        return checks.rel_err(o.X, Xs) > 1e-6 or np.abs(o.Pinv @ (B.T @ B) - np.eye(o.rank)).max() > 1e-6
+
+    assert not pins_fail(fp64.solve(A, Y, tol=1e-10, variant=variant))
+    assert pins_fail(fp64.solve(A, Y, tol=1e-10, variant=variant, mutation=mutation))
 
 
 def test_ill_conditioned_generator_growth_and_the_method_noise_floor():
