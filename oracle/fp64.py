@@ -26,11 +26,15 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile rg_oracle.c (plain -O2, OpenMP only across batched instances)."""
+    """Compile rg_oracle.c (plain -O2, OpenMP only across batched instances). Floating-point
+    contraction is off: every product and sum rounds on its own, as the paper's NumPy
+    implementation does, so the oracle gives bit-identical results on x86 and Arm hosts
+    (GCC fuses a * b + c into one FMA by default on aarch64, not on x86-64 at -O2)."""
     os.makedirs(BUILD_DIR, exist_ok=True)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(SRC),
+                                                                       os.path.getmtime(__file__)):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99", SRC, "-o", tmp, "-lm"]
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=c99", SRC, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB)
     return LIB
@@ -54,6 +58,10 @@ def lib():
             L.rgo_solve_batch.argtypes = [i64, i64p, i64p, i64p, f64p, f64p, ctypes.c_double,
                                           ctypes.c_int, ctypes.c_int, f64p, i64p, ctypes.c_void_p]
             L.rgo_solve_batch.restype = ctypes.c_int
+            L.rgo_solve_batch_var.argtypes = [i64, i64p, i64p, i64p, f64p, f64p, ctypes.c_double,
+                                              ctypes.c_int, ctypes.c_int, ctypes.c_int, f64p,
+                                              i64p, ctypes.c_void_p, u8p]
+            L.rgo_solve_batch_var.restype = ctypes.c_int
             L.rgo_pinv_mut.argtypes = [i64, i64, f64p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                        f64p, i64p, u8p]
             L.rgo_pinv_mut.restype = ctypes.c_int
@@ -128,21 +136,30 @@ def pinv(A, tol: float = 1e-10, test_mode: int = TEST_REL, mutation: int = 0):
 
 
 def solve_batch(A_packed, Y_packed, row_off, elem_off, x_off, tol: float = 1e-10,
-                test_mode: int = TEST_REL, threads: int = 0):
-    """Batched oracle (OpenMP over instances). Returns (X_packed, ranks)."""
+                test_mode: int = TEST_REL, threads: int = 0, variant: int = GENERAL,
+                with_indep: bool = False):
+    """Batched oracle (OpenMP over instances). Returns (X_packed, ranks), or
+    (X_packed, ranks, indep_packed) with with_indep (per-row flags packed by row_off; rows
+    after a capacity stop hold 0xFF). A capacity stop (status 4) is allowed; other failures
+    raise."""
     A = np.ascontiguousarray(A_packed, dtype=np.float64)
     Y = np.ascontiguousarray(Y_packed, dtype=np.float64)
     ro = np.ascontiguousarray(row_off, dtype=np.int64)
     eo = np.ascontiguousarray(elem_off, dtype=np.int64)
     xo = np.ascontiguousarray(x_off, dtype=np.int64)
     B = ro.shape[0] - 1
-    X = np.zeros(int(xo[-1]))
-    ranks = np.zeros(B, dtype=np.int64)
-    status = np.zeros(B, dtype=np.int32)
-    st = lib().rgo_solve_batch(B, _ptr(ro), _ptr(eo), _ptr(xo), _ptr(A), _ptr(Y), float(tol),
-                               int(test_mode), int(threads), _ptr(X), _ptr(ranks), _ptr(status))
-    if st != 0:
-        raise RuntimeError(f"rgo_solve_batch failed: statuses {np.unique(status)}")
+    X = np.zeros(max(int(xo[-1]), 1))
+    ranks = np.zeros(max(B, 1), dtype=np.int64)
+    status = np.zeros(max(B, 1), dtype=np.int32)
+    indep = np.zeros(max(int(ro[-1]), 1), dtype=np.uint8) if with_indep else None
+    lib().rgo_solve_batch_var(B, _ptr(ro), _ptr(eo), _ptr(xo), _ptr(A), _ptr(Y), float(tol),
+                              int(test_mode), int(variant), int(threads), _ptr(X), _ptr(ranks),
+                              _ptr(status), _ptr(indep))
+    if B and not np.isin(status[:B], (0, 4)).all():
+        raise RuntimeError(f"rgo_solve_batch failed: statuses {np.unique(status[:B])}")
+    X, ranks = X[:int(xo[-1])], ranks[:B]
+    if with_indep:
+        return X, ranks, indep[:int(ro[-1])]
     return X, ranks
 
 

@@ -374,9 +374,18 @@ int rgo_pinv(int64_t n, int64_t m, const double *A, double tol, int test_mode, d
  * X[x_off[b] .. x_off[b] + m_b)). Instances run in parallel over `threads` OpenMP
  * threads (<= 0: all available). ranks (B) and status (B) may be NULL.
  */
-int rgo_solve_batch(int64_t B, const int64_t *row_off, const int64_t *elem_off,
-                    const int64_t *x_off, const double *A, const double *Y, double tol,
-                    int test_mode, int threads, double *X, int64_t *ranks, int *status) {
+/*
+ * Batched form: B independent streams (OpenMP over instances, one thread per instance).
+ * Instance b's rows are A[elem_off[b] .. elem_off[b+1]) viewed as n_b x m_b row-major with
+ * n_b = row_off[b+1] - row_off[b], m_b = x_off[b+1] - x_off[b]; its targets are
+ * Y[row_off[b] ..]. Outputs: X at x_off[b], ranks[b], status[b] and, when indep is not
+ * NULL, the per-row flags at indep[row_off[b] ..] (rows after a capacity stop keep 0xFF).
+ * variant as rgo_solve_var. Each instance runs rgo_solve_var unchanged, with r_max = m_b.
+ */
+int rgo_solve_batch_var(int64_t B, const int64_t *row_off, const int64_t *elem_off,
+                        const int64_t *x_off, const double *A, const double *Y, double tol,
+                        int test_mode, int variant, int threads, double *X, int64_t *ranks,
+                        int *status, uint8_t *indep) {
   if (B < 0 || !row_off || !elem_off || !x_off) return 1;
   int bad = 0;
 #ifdef _OPENMP
@@ -388,14 +397,24 @@ int rgo_solve_batch(int64_t B, const int64_t *row_off, const int64_t *elem_off,
     int64_t m = x_off[b + 1] - x_off[b];
     int64_t rk = 0;
     int st = 1;
+    uint8_t *ind = indep ? indep + row_off[b] : NULL;
+    if (ind)
+      for (int64_t i = 0; i < n; ++i) ind[i] = 0xFF;
     if (m > 0 && (elem_off[b + 1] - elem_off[b]) == n * m)
-      st = rgo_solve(n, m, A + elem_off[b], Y + row_off[b], tol, test_mode, m, X + x_off[b],
-                     &rk, NULL, NULL, NULL, NULL, NULL, NULL);
+      st = rgo_solve_var(n, m, A + elem_off[b], Y + row_off[b], tol, test_mode, m, variant, 0,
+                         X + x_off[b], &rk, NULL, ind, NULL, NULL, NULL, NULL);
     if (ranks) ranks[b] = rk;
     if (status) status[b] = st;
     bad |= (st != 0);
   }
   return bad ? 1 : 0;
+}
+
+int rgo_solve_batch(int64_t B, const int64_t *row_off, const int64_t *elem_off,
+                    const int64_t *x_off, const double *A, const double *Y, double tol,
+                    int test_mode, int threads, double *X, int64_t *ranks, int *status) {
+  return rgo_solve_batch_var(B, row_off, elem_off, x_off, A, Y, tol, test_mode, 0, threads, X,
+                             ranks, status, NULL);
 }
 
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */

@@ -150,6 +150,18 @@ def test_uneven_batch_sample_rank_and_batch_form():
         assert ranks[k] == r[b]
         one = fp64.solve(s.A, s.Y, tol=1e-10)
         np.testing.assert_array_equal(X[xo[k]:xo[k + 1]], one.X)  # same code, same order
+    # the flag-returning form, in both variants: per-instance flags and X as the
+    # single-stream oracle gives them; the orthonormal flags equal the general ones and
+    # the prefix-rank growth of the generator (first r rows grow the rank)
+    for variant in (fp64.GENERAL, fp64.ORTHONORMAL):
+        Xv, rv, iv = fp64.solve_batch(A, Y, ro, eo, xo, tol=1e-10, threads=2, variant=variant,
+                                      with_indep=True)
+        for k, (b, s) in enumerate(zip([0, 1, 2, 3, 17, 101], bt.streams)):
+            one = fp64.solve(s.A, s.Y, tol=1e-10, variant=variant)
+            np.testing.assert_array_equal(iv[ro[k]:ro[k + 1]], one.indep)
+            np.testing.assert_array_equal(Xv[xo[k]:xo[k + 1]], one.X)
+            assert rv[k] == one.rank == r[b]
+            assert list(np.flatnonzero(one.indep)) == list(range(r[b]))
 
 
 # ---------------------------------------------------------------------------
