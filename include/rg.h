@@ -282,23 +282,25 @@ rg_status rg_batch_reset(rg_batch* bt);
 rg_status rg_batch_free(rg_batch* bt);
 
 /*
- * rg_solve_noalloc -- solve one stream from scratch (Algorithm 1 over the n rows, as
- * rg_init + rg_add_rows + rg_solution would) WITHOUT allocating any memory. The paper has
- * no counterpart: this entry point exists for callers that cannot call cudaMalloc, for
- * example a latency-critical loop that cannot accept cudaMalloc's implicit device
- * synchronisation, or a host application whose device memory is owned entirely by its own
- * allocator.
+ * rg_solve_noalloc -- solve one stream from scratch, as rg_init + rg_add_rows + rg_solution
+ * would, WITHOUT allocating any memory. The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc, for example a latency-critical loop that
+ * cannot accept cudaMalloc's implicit device synchronisation, or a host application whose
+ * device memory is owned entirely by its own allocator.
  *   Gamma      device, n x m row-major FP64;  y  device, n FP64 targets;  n >= 0.
  *   m, tol, flags, r_max: as rg_init.
  *   X          device, m FP64: receives the minimum-norm least-squares solution.
  *   rank_out   host, may be NULL. When given, the call synchronises the stream, stores the
- *              rank and returns any device-side error (non-finite row, capacity); when
- *              NULL the call is asynchronous and device-side errors are not reported.
+ *              rank and returns any device-side error (non-finite row, capacity). When NULL
+ *              the call is asynchronous and device-side errors of this call cannot be read
+ *              at all (the next call clears the status word). Pass NULL while the stream is
+ *              being captured: the synchronisation is not allowed during a capture.
  *   cuda_stream  cudaStream_t for all work (NULL: legacy default stream).
  * State and scratch live in one fixed file-scope device array of 8 MiB that every GPU
  * loading the library holds until the process exits; a problem whose state and scratch do
- * not fit (with r_max = m: m above 494 in FP64, above 528 in mixed mode; a smaller r_max
- * raises the limit) is rejected with RG_EINVAL and a message.
+ * not fit is rejected with RG_EINVAL and a message. With r_max = m the limits are m <= 494
+ * in FP64, m <= 568 in FP64 with RG_ORTHONORMAL (no dual basis to keep) and m <= 528 in
+ * mixed mode; a smaller r_max raises them.
  * Every call shares that array and clears what must start at zero itself; calls that
  * overlap on the GPU (different streams or host threads) race on it and must be
  * serialised by the caller. The first call on each device looks up the array's device

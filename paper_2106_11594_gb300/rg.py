@@ -113,11 +113,34 @@ def _need_cuda():
 def solve_noalloc(Gamma, y, X, tol: float = 1e-10, mode: int = RG_FP64,
                   test: int = RG_TEST_REL, r_max: int = 0, stream=None, with_rank: bool = True):
     """rg_solve_noalloc: one stream from scratch with no allocation inside the library.
-    Gamma (n, m), y (n,), X (m,) are float64 CUDA tensors. Returns the rank (synchronising)
-    or None when with_rank is False (asynchronous)."""
+    Gamma (n, m), y (n,), X (m,) are contiguous float64 CUDA tensors on the current device.
+    Returns the rank (synchronising) or None when with_rank is False (asynchronous; device
+    errors of the call are then not reported). Arguments that do not match that contract
+    raise RGError(RG_EINVAL) before anything is launched."""
+    import torch
+
+    def bad(msg):
+        raise RGError(RG_EINVAL, "rg_solve_noalloc", msg)
+
+    for name, t in (("Gamma", Gamma), ("y", y), ("X", X)):
+        if not isinstance(t, torch.Tensor):
+            bad(f"{name} is not a tensor")
+        if t.dtype != torch.float64:
+            bad(f"{name} has dtype {t.dtype}, float64 required")
+        if not t.is_contiguous():
+            bad(f"{name} is not contiguous")
+    if Gamma.dim() != 2:
+        bad(f"Gamma has {Gamma.dim()} dimensions, 2 required")
+    n, m = int(Gamma.shape[0]), int(Gamma.shape[1])
+    if y.numel() != n:
+        bad(f"y has {y.numel()} elements, Gamma has {n} rows")
+    if X.numel() < m:
+        bad(f"X has {X.numel()} elements, fewer than m = {m}")
     _need_cuda()
-    n = Gamma.shape[0]
-    m = Gamma.shape[1]
+    cur = torch.cuda.current_device()
+    for name, t in (("Gamma", Gamma), ("y", y), ("X", X)):
+        if t.device.type != "cuda" or t.device.index != cur:
+            bad(f"{name} is on {t.device}, not on the current CUDA device {cur}")
     r = ctypes.c_int64(0)
     _check(lib().rg_solve_noalloc(_ptr(Gamma), _ptr(y), n, m, float(tol), int(mode) | int(test),
                                   int(r_max), _ptr(X), ctypes.byref(r) if with_rank else None,

@@ -34,3 +34,25 @@ def test_version_string_without_gpu():
     L = rg.lib()
     assert b"sm_103a" in L.rg_version()
     assert L.rg_last_error() == b""
+
+
+def test_noalloc_binding_rejects_bad_arguments_before_any_launch():
+    """rg_solve_noalloc takes raw pointers, so the binding checks dtype, shape and
+    contiguity first: a float32 or short X would otherwise be written past its end."""
+    import pytest
+    import torch
+    G = torch.zeros((4, 8), dtype=torch.float64)
+    y = torch.zeros(4, dtype=torch.float64)
+    X = torch.zeros(8, dtype=torch.float64)
+    bad_cases = [
+        (G.float(), y, X),                              # Gamma float32
+        (G, y, X.float()),                              # X float32
+        (G, y, torch.zeros(7, dtype=torch.float64)),    # X shorter than m
+        (G, torch.zeros(3, dtype=torch.float64), X),    # y length != n
+        (G.reshape(-1), y, X),                          # Gamma not 2-D
+        (torch.zeros((8, 4), dtype=torch.float64).t(), y, X),  # Gamma not contiguous
+    ]
+    for g_, y_, x_ in bad_cases:
+        with pytest.raises(rg.RGError) as ei:
+            rg.solve_noalloc(g_, y_, x_)
+        assert ei.value.code == rg.RG_EINVAL

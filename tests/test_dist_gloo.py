@@ -1,5 +1,7 @@
 """Multi-process host logic on CPU (gloo, world size 2): the instance partition of a
-batch and the whole-job throughput (units of all ranks over the slowest rank's time)."""
+batch, the whole-job throughput (units of all ranks over the slowest rank's time) and the
+sharded batch itself: the instances a rank draws are bit-identical to the same instances
+of the unsharded batch (every instance is seeded by its own id)."""
 import os
 import socket
 
@@ -11,6 +13,10 @@ import torch.multiprocessing as mp
 
 from paper_2106_11594_gb300 import dist as rgdist
 from paper_2106_11594_gb300 import inputs
+
+
+# small uneven shapes (n, m, r) for the sharded-batch identity check
+SMALL_SHAPES = [(40 + 7 * b, 8 + (5 * b) % 29, 2 + b % 5) for b in range(13)]
 
 
 def _free_port():
@@ -35,8 +41,22 @@ def _worker(rank, world, port, out_dir):
         rows_mine = float(n[mine].sum())
         ms_mine = 10.0 + 5.0 * rank  # rank 1 is the slower one
         rate, ms, units = rgdist.job_throughput(rows_mine, ms_mine)
+        # the bench's sharded batch: this rank's share, drawn on its own, equals the same
+        # instances cut out of the whole batch, bit for bit
+        import bench
+        cpu = torch.device("cpu")
+        bat = bench.BatchOnGpu(SMALL_SHAPES, 3, 1e-4, cpu, world, rank)
+        full = bench.BatchOnGpu(SMALL_SHAPES, 3, 1e-4, cpu, 1, 0)
+        ident = True
+        for k, i in enumerate(bat.ids):
+            ident &= torch.equal(bat.A[bat.eo[k]:bat.eo[k + 1]], full.A[full.eo[i]:full.eo[i + 1]])
+            ident &= torch.equal(bat.Y[bat.ro[k]:bat.ro[k + 1]], full.Y[full.ro[i]:full.ro[i + 1]])
+        cover = torch.zeros(len(SMALL_SHAPES), dtype=torch.int64)
+        cover[torch.tensor(bat.ids, dtype=torch.int64)] = 1
+        dist.all_reduce(cover)
         np.save(os.path.join(out_dir, f"r{rank}.npy"),
-                np.array([rate, ms, units, float(same), float(len(mine))]))
+                np.array([rate, ms, units, float(same), float(len(mine)), float(ident),
+                          float((cover == 1).all()), float(len(bat.ids))]))
     finally:
         dist.destroy_process_group()
 
@@ -74,8 +94,11 @@ def test_gloo_two_ranks(tmp_path):
     n, m, r = inputs.uneven_batch_shapes(256)
     total_rows = float(n.sum())
     for v in res:
-        rate, ms, units, same, cnt = v
+        rate, ms, units, same, cnt, ident, cover, nb = v
         assert same == 1.0
+        assert ident == 1.0  # a rank's instances equal the unsharded batch's
+        assert cover == 1.0  # every instance on exactly one rank
+        assert 0 < nb < len(SMALL_SHAPES)
         assert ms == 15.0  # the slowest rank's time
         assert units == total_rows  # every instance counted once
         assert rate == pytest.approx(total_rows / 0.015)

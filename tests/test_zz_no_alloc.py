@@ -3,14 +3,14 @@ cudaMalloc (a latency-critical loop that cannot take cudaMalloc's implicit devic
 synchronisation, or a host whose device memory belongs to its own allocator).
 
 Checked through the C ABI against the allocating entry points (rg_init, rg_add_rows,
-rg_solution) on two calls in a row: the second call reuses the fixed device array that the
-first one left behind, so it also checks that each call clears what must start at zero.
-This file is collected last on purpose."""
+rg_solution) and directly against the CPU oracle, on two calls in a row: the second call
+reuses the fixed device array that the first one left behind, so it also checks that each
+call clears what must start at zero. This file is collected last on purpose."""
 import numpy as np
 import pytest
 
 from gpu_helpers import run_stream, torch_cuda
-from oracle import checks
+from oracle import checks, fp64
 from paper_2106_11594_gb300 import inputs, rg
 
 pytestmark = pytest.mark.gpu
@@ -33,6 +33,9 @@ def test_noalloc_matches_allocating_api_two_calls_in_a_row():
         ref = run_stream(s.A, s.Y, s.n, export=False)
         assert rank == ref["rank"]
         assert checks.rel_err(X, ref["X"]) <= 1e-10
+        o = fp64.solve(s.A, s.Y, tol=1e-10)  # and the oracle itself
+        assert rank == o.rank == s.rank
+        assert checks.rel_err(X, o.X) <= 1e-10
 
 
 def test_noalloc_mixed_matches_allocating_api():
@@ -42,6 +45,24 @@ def test_noalloc_mixed_matches_allocating_api():
         ref = run_stream(s.A, s.Y, s.n, mode=rg.RG_MIXED, export=False)
         assert rank == ref["rank"] == 20
         assert checks.rel_err(X, ref["X"]) <= 1e-4
+        o = fp64.solve(s.A, s.Y, tol=1e-10, variant=fp64.ORTHONORMAL)
+        assert checks.rel_err(X, o.X) <= 1e-4
+
+
+def test_noalloc_asynchronous_call_matches_synchronous():
+    """rank_out NULL: the call returns without waiting; after a synchronisation X equals
+    the synchronous call's, bit for bit (same kernels, same order)."""
+    torch, dev = torch_cuda()
+    s = inputs.large_stream(2048, 128, 16)
+    At = torch.from_numpy(s.A).to(dev)
+    Yt = torch.from_numpy(s.Y).to(dev)
+    X1 = torch.full((128,), np.nan, dtype=torch.float64, device=dev)
+    X2 = torch.full((128,), np.nan, dtype=torch.float64, device=dev)
+    assert rg.solve_noalloc(At, Yt, X1) == 16
+    assert rg.solve_noalloc(At, Yt, X2, with_rank=False) is None
+    torch.cuda.synchronize()
+    assert torch.equal(X1, X2)
+    assert checks.rel_err(X2.cpu().numpy(), fp64.solve(s.A, s.Y, tol=1e-10).X) <= 1e-10
 
 
 def test_noalloc_rejects_sizes_beyond_the_fixed_array():
