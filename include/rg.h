@@ -60,11 +60,16 @@ enum {
   RG_TEST_REL = 0,    /* independent iff ||Gamma_r|| > eps ||Gamma||                  */
   RG_TEST_PAPER = 2,  /* dependent iff ||Gamma_r|| < eps or ||Gamma_r|| < eps ||Gamma||
                          (Eq. label_eq_eps, both clauses)                            */
-  RG_ORTHONORMAL = 4  /* keep the orthonormal variant of Section 2.2 (alpha_{n+1} =
+  RG_ORTHONORMAL = 4, /* keep the orthonormal variant of Section 2.2 (alpha_{n+1} =
                          1/||Gamma_r||: the basis rows are orthonormal and serve as their
                          own dual basis) instead of Algorithm 1's raw rows and dual basis.
                          RG_MIXED always uses it; with RG_FP64 it is opt-in (rg_init,
                          rg_solve_noalloc and rg_batch_init)                         */
+  RG_ORTHOGONAL = 8   /* keep the orthogonal variant of Section 2.2 (alpha_{n+1} = 1: the
+                         basis rows are the raw rejections Gamma_r, mutually orthogonal, and
+                         the dual rows are Gamma_r / ||Gamma_r||^2; appends leave the older
+                         rows unchanged). FP64 only: excludes RG_MIXED and
+                         RG_ORTHONORMAL (RG_EINVAL)                                  */
 };
 
 /*
@@ -75,7 +80,7 @@ enum {
  *              paper's default (m^2 r + m r + m) eps_M, r the rank before the row.
  *              Must not be NaN.
  *   flags      RG_FP64 or RG_MIXED, OR-ed with RG_TEST_REL or RG_TEST_PAPER and
- *              optionally RG_ORTHONORMAL. In RG_MIXED mode a row whose FP32 relative rejection
+ *              optionally RG_ORTHONORMAL or (FP64 only) RG_ORTHOGONAL. In RG_MIXED mode a row whose FP32 relative rejection
  *              ||Gamma_r|| / ||Gamma|| exceeds 1e-5 is recomputed and decided in FP64;
  *              rows below that floor are taken as dependent.
  *   r_max      capacity of the basis (maximum rank), 1..m; <= 0 means m.
@@ -196,6 +201,39 @@ rg_status rg_reset(rg_state* st);
  */
 rg_status rg_export(rg_state* st, double* C, double* Ct, double* Pinv, double* w,
                     int64_t* basis_rows, int64_t capacity, int64_t* rank_out);
+
+/*
+ * Snapshots of the factorization: checkpoint / resume of a stream, and the factor
+ * snapshots that gradients through intermediate solutions X_n need. The paper has no
+ * counterpart; the state copied is exactly what Algorithm 1 carries from one row to the
+ * next (the basis, its dual basis, the r x r state and the solution coordinates, Section
+ * 2.1), so that restoring a snapshot taken after n rows and feeding rows n+1.. gives the
+ * same results as never having stopped.
+ *
+ * rg_snapshot_size -- bytes of a snapshot of this state (host; fixed by m, r_max and the
+ *   flags given to rg_init: about 8 r_max (2m + r_max) bytes in FP64 mode).
+ */
+rg_status rg_snapshot_size(rg_state* st, int64_t* bytes_out);
+
+/*
+ * rg_snapshot -- copy the state into buf: the basis C (or Q), the dual basis Ct (general
+ * variant), the FP32 copy of Q (mixed mode), the leading r x r block of P = B^T B, the
+ * solution coordinates w_b and u, the basis-row indices, the rank, the rows seen and the
+ * internal block size. A deferred update of the previous call is folded into the state
+ * first. The rank is read on the device; only rows below it are copied.
+ *   buf    device, 256-byte aligned, at least rg_snapshot_size bytes; owned by the caller.
+ * Asynchronous; the snapshot is complete when the state's stream reaches this point.
+ */
+rg_status rg_snapshot(rg_state* st, void* buf, int64_t bytes);
+
+/*
+ * rg_restore -- make the state equal to a snapshot taken from a state with the same m,
+ * r_max and flags (this state or another); the next rows continue from it. A buffer
+ * whose header does not match (another shape or variant, or not a snapshot) leaves the
+ * state unchanged and returns RG_EINVAL at the next synchronising call. Clears the status
+ * word. Asynchronous.
+ */
+rg_status rg_restore(rg_state* st, const void* buf, int64_t bytes);
 
 /* rg_set_stream -- enqueue later work of this state on another cudaStream_t. */
 rg_status rg_set_stream(rg_state* st, void* cuda_stream);

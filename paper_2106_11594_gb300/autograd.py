@@ -66,3 +66,66 @@ def lstsq_rg_batch(A_packed, y_packed, row_offsets, elem_offsets, m_list, tol: f
     """X_packed (instances back to back by m_b) for a packed batch (rg_batch_add_rows
     layout), differentiable in A_packed and y_packed."""
     return _LstsqRGBatch.apply(A_packed, y_packed, row_offsets, elem_offsets, list(m_list), tol, mode)
+
+
+class _LstsqRGPath(torch.autograd.Function):
+    """X_n = A_n^+ y_n at several row counts n_1 < n_2 < ... of one stream. The forward
+    feeds the rows once and takes a factor snapshot (rg_snapshot) at every n_i; the
+    backward restores each snapshot into a scratch state and runs the adjoint kernel on
+    the rows [0, n_i), so the gradient of a loss on intermediate solutions needs no second
+    pass over the stream."""
+
+    @staticmethod
+    def forward(ctx, A, y, counts, tol, mode):
+        A = A.contiguous()
+        y = y.contiguous()
+        m = A.shape[1]
+        st = rg.RankGreville(m, tol, mode)
+        Xs = torch.empty((len(counts), m), dtype=torch.float64, device=A.device)
+        snaps = []
+        prev = 0
+        for i, n_i in enumerate(counts):
+            if n_i > prev:
+                st.add_rows(A[prev:n_i], y[prev:n_i])
+            st.solution(Xs[i], with_rank=False)
+            buf = st.new_snapshot_buffer(A.device)
+            st.snapshot(buf)
+            snaps.append(buf)
+            prev = n_i
+        st.sync()
+        st.close()
+        ctx.snaps = snaps
+        ctx.counts = counts
+        ctx.tol, ctx.mode = tol, mode
+        ctx.save_for_backward(A, y)
+        return Xs
+
+    @staticmethod
+    def backward(ctx, gX):
+        A, y = ctx.saved_tensors
+        gA = torch.zeros_like(A)
+        gy = torch.zeros_like(y)
+        st = rg.RankGreville(A.shape[1], ctx.tol, ctx.mode)
+        for i, n_i in enumerate(ctx.counts):
+            g = gX[i].contiguous()
+            if n_i == 0 or not bool(torch.any(g != 0)):
+                continue
+            st.restore(ctx.snaps[i])
+            gA_i = torch.empty((n_i, A.shape[1]), dtype=torch.float64, device=A.device)
+            gy_i = torch.empty(n_i, dtype=torch.float64, device=A.device)
+            st.adjoint(A[:n_i], y[:n_i], g, gA_i, gy_i)
+            gA[:n_i] += gA_i
+            gy[:n_i] += gy_i
+        st.sync()
+        st.close()
+        return gA, gy, None, None, None
+
+
+def lstsq_rg_path(A, y, counts, tol: float = 1e-10, mode: int = rg.RG_FP64):
+    """Solutions X_{n_i} = A_{n_i}^+ y_{n_i} after the first n_i rows, for increasing row
+    counts `counts`, as a (len(counts), m) tensor differentiable in A and y (gradients flow
+    through every intermediate solution via factor snapshots)."""
+    counts = [int(c) for c in counts]
+    if any(b <= a for a, b in zip(counts, counts[1:])) or (counts and (counts[0] < 0 or counts[-1] > A.shape[0])):
+        raise ValueError("counts must increase strictly and lie in [0, n]")
+    return _LstsqRGPath.apply(A, y, counts, tol, mode)

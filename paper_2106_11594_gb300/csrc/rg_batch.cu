@@ -23,7 +23,7 @@
 namespace rg {
 
 struct BatchDev {
-  int B, mixed, ortho, test_mode, kb_max, ld_max, r_max_max, nmc_max;
+  int B, mixed, ortho, orthog, test_mode, kb_max, ld_max, r_max_max, nmc_max;
   int kb_cap;  // rows of block scratch laid out per CTA (kb_max <= kb_cap)
   double tol, tau_lo;
   const int* m;               // B
@@ -131,7 +131,7 @@ __host__ __device__ inline size_t scratch_layout(int kb, int ldm, int rmm, int n
 // CTA's tensor-core context: one mbarrier and TC_TMEM_COLS columns of tensor memory (one
 // CTA per SM in mixed mode, so the 512 columns of an SM always suffice). FP64 mode runs two
 // CTAs per SM; mixed mode one, with the register budget that its staging needs.
-template <bool MIXED, bool ORTHO>
+template <bool MIXED, int VAR>
 __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, const double* __restrict__ Gp,
                                                    const int64_t* __restrict__ roff,
                                                    const int64_t* __restrict__ eoff,
@@ -173,8 +173,10 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, co
   S.tcx = MIXED ? (void*)&tcx : nullptr;
   S.Rs = reinterpret_cast<double*>(dyn_base);
   S.rs_cap = ((MIXED ? TC_SMEM_MIXED : TC_SMEM) - 1024) / 8;
+  constexpr bool ORTHO = VAR == VAR_ORTHONORMAL;
   S.mixed = MIXED;
   S.ortho = ORTHO;
+  S.orthog = VAR == VAR_ORTHOGONAL;
   S.test_mode = D.test_mode;
   S.tol = D.tol;
   S.tau_lo = D.tau_lo;
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, co
     S.ctrl = D.ctrl + (size_t)b * CTRL_N;
     S.rows_seen = D.rows_seen + b;
     CallArgs A{Gp + eoff[b], yp + roff[b], n, indep ? indep + roff[b] : nullptr};
-    const bool ok = process_rows<CtaTeam, MIXED, ORTHO>(CtaTeam{}, S, A);
+    const bool ok = process_rows<CtaTeam, MIXED, VAR>(CtaTeam{}, S, A);
     __syncthreads();
     if (threadIdx.x == 0) {
       const int st = ld_acquire_i32(S.ctrl + CTRL_STATUS);
@@ -224,9 +226,11 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, co
 }
 
 // FP32 projections always come with the orthonormal variant.
-static const void* batch_kernel_ptr(int mixed, int ortho) {
-  if (mixed) return (const void*)batch_kernel<true, true>;
-  return ortho ? (const void*)batch_kernel<false, true> : (const void*)batch_kernel<false, false>;
+static const void* batch_kernel_ptr(int mixed, int ortho, int orthog) {
+  if (mixed) return (const void*)batch_kernel<true, VAR_ORTHONORMAL>;
+  if (ortho) return (const void*)batch_kernel<false, VAR_ORTHONORMAL>;
+  if (orthog) return (const void*)batch_kernel<false, VAR_ORTHOGONAL>;
+  return (const void*)batch_kernel<false, VAR_GENERAL>;
 }
 
 // Longest-first order of the instances for this call (single CTA, bitonic sort in shared
@@ -335,6 +339,7 @@ __global__ void __launch_bounds__(NT, 2) batch_adjoint_kernel(BatchDev D, const 
     S.r_max = D.r_max[b];
     S.mixed = D.mixed;
     S.ortho = D.ortho;
+    S.orthog = D.orthog;
     S.ctrl = D.ctrl + (size_t)b * CTRL_N;
     inst_layout(m, S.ld, S.r_max, D.mixed, D.ortho, D.state + D.soff[b], &S);
     const int r = D.ctrl[(size_t)b * CTRL_N + CTRL_R];
@@ -414,7 +419,10 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
   if (B <= 0 || B > (1 << 20)) return fail(RG_EINVAL, "rg_batch_init: B = %lld out of range", (long long)B);
   if (!m) return fail(RG_EINVAL, "rg_batch_init: m is NULL");
   if (std::isnan(tol)) return fail(RG_EINVAL, "rg_batch_init: tol is NaN");
-  if (flags & ~(RG_MIXED | RG_TEST_PAPER | RG_ORTHONORMAL)) return fail(RG_EINVAL, "rg_batch_init: unknown flags %d", flags);
+  if (flags & ~(RG_MIXED | RG_TEST_PAPER | RG_ORTHONORMAL | RG_ORTHOGONAL))
+    return fail(RG_EINVAL, "rg_batch_init: unknown flags %d", flags);
+  if ((flags & RG_ORTHOGONAL) && (flags & (RG_MIXED | RG_ORTHONORMAL)))
+    return fail(RG_EINVAL, "rg_batch_init: RG_ORTHOGONAL excludes RG_MIXED and RG_ORTHONORMAL");
   rg_batch* bt = new (std::nothrow) rg_batch();
   if (!bt) return fail(RG_ENOMEM, "rg_batch_init: host allocation failed");
   bt->m.resize(B);
@@ -442,6 +450,7 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
   D.B = (int)B;
   D.mixed = (flags & RG_MIXED) ? 1 : 0;
   D.ortho = (flags & (RG_MIXED | RG_ORTHONORMAL)) ? 1 : 0;
+  D.orthog = (flags & RG_ORTHOGONAL) ? 1 : 0;
   D.test_mode = (flags & RG_TEST_PAPER) ? 2 : 0;
   D.tol = tol;
   D.tau_lo = 1e-5;
@@ -455,7 +464,7 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
   int nsm = 0, per = 0;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, bt->device);
   const int dyn = D.mixed ? TC_SMEM_MIXED : TC_SMEM;
-  const void* kfn = batch_kernel_ptr(D.mixed, D.ortho);
+  const void* kfn = batch_kernel_ptr(D.mixed, D.ortho, D.orthog);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
   if (e == cudaSuccess)  // up to two CTAs of ~105 KiB each per SM
     e = cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -527,6 +536,7 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
 
 rg_status rg_batch_add_rows(rg_batch* bt, const double* Gamma_packed, const int64_t* row_offsets,
                             const int64_t* elem_offsets, const double* y_packed, uint8_t* indep_out) {
+  NvtxRange nvtx_range("rg_batch_add_rows");
   if (!valid_batch(bt)) return fail(RG_EINVAL, "rg_batch_add_rows: invalid batch");
   if (!Gamma_packed || !row_offsets || !elem_offsets || !y_packed)
     return fail(RG_EINVAL, "rg_batch_add_rows: NULL argument");
@@ -542,20 +552,24 @@ rg_status rg_batch_add_rows(rg_batch* bt, const double* Gamma_packed, const int6
     // kernel writes every applied row and the rest are left as the caller initialised them
   }
   if (D.mixed)
-    batch_kernel<true, true><<<bt->grid, NT, TC_SMEM_MIXED, bt->stream>>>(D, Gamma_packed, row_offsets,
-                                                                   elem_offsets, y_packed, indep_out);
+    batch_kernel<true, VAR_ORTHONORMAL><<<bt->grid, NT, TC_SMEM_MIXED, bt->stream>>>(
+        D, Gamma_packed, row_offsets, elem_offsets, y_packed, indep_out);
   else if (D.ortho)
-    batch_kernel<false, true><<<bt->grid, NT, TC_SMEM, bt->stream>>>(D, Gamma_packed, row_offsets,
-                                                               elem_offsets, y_packed, indep_out);
+    batch_kernel<false, VAR_ORTHONORMAL><<<bt->grid, NT, TC_SMEM, bt->stream>>>(
+        D, Gamma_packed, row_offsets, elem_offsets, y_packed, indep_out);
+  else if (D.orthog)
+    batch_kernel<false, VAR_ORTHOGONAL><<<bt->grid, NT, TC_SMEM, bt->stream>>>(
+        D, Gamma_packed, row_offsets, elem_offsets, y_packed, indep_out);
   else
-    batch_kernel<false, false><<<bt->grid, NT, TC_SMEM, bt->stream>>>(D, Gamma_packed, row_offsets,
-                                                                elem_offsets, y_packed, indep_out);
+    batch_kernel<false, VAR_GENERAL><<<bt->grid, NT, TC_SMEM, bt->stream>>>(
+        D, Gamma_packed, row_offsets, elem_offsets, y_packed, indep_out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "rg_batch_add_rows: launch");
   return RG_OK;
 }
 
 rg_status rg_batch_solution(rg_batch* bt, double* X_packed, const int64_t* x_offsets, int64_t* ranks_out) {
+  NvtxRange nvtx_range("rg_batch_solution");
   if (!valid_batch(bt)) return fail(RG_EINVAL, "rg_batch_solution: invalid batch");
   if (!X_packed) return fail(RG_EINVAL, "rg_batch_solution: X is NULL");
   batch_solution_kernel<<<bt->grid, NT, 0, bt->stream>>>(bt->D, X_packed, x_offsets, ranks_out);
@@ -590,6 +604,7 @@ rg_status rg_batch_adjoint(rg_batch* bt, const double* Gamma_packed, const int64
                            const int64_t* elem_offsets, const double* y_packed, int64_t total_rows,
                            const double* g_packed, const int64_t* x_offsets, double* gA_packed,
                            double* gy_packed) {
+  NvtxRange nvtx_range("rg_batch_adjoint");
   if (!valid_batch(bt)) return fail(RG_EINVAL, "rg_batch_adjoint: invalid batch");
   if (total_rows < 0) return fail(RG_EINVAL, "rg_batch_adjoint: total_rows < 0");
   if (!row_offsets || !elem_offsets || !g_packed || (total_rows > 0 && (!Gamma_packed || !y_packed || !gA_packed || !gy_packed)))

@@ -42,9 +42,10 @@ struct CallArgs {
 
 struct GridTeam {
   int* ctrl;
+  int bar_off = CTRL_BAR_COUNT;  // control word of the barrier's arrival counter
   __device__ __forceinline__ int id() const { return blockIdx.x; }
   __device__ __forceinline__ int size() const { return gridDim.x; }
-  __device__ __forceinline__ bool sync() const { return grid_barrier(ctrl); }
+  __device__ __forceinline__ bool sync() const { return grid_barrier(ctrl, bar_off); }
 };
 
 struct CtaTeam {
@@ -560,10 +561,38 @@ __device__ void decide_rows_team(const Team& T, const StreamDev& S, const CallAr
 // Dependent rows: P += gamma gamma^T, u += gamma D for rows of a run whose D are in S.Dall.
 // =======================================================================================
 
+// Compensated FP32 accumulation for mixed mode's Gram sums: blocked summation (FABsum;
+// Blanchard, Higham and Mary, "A class of fast and accurate summation algorithms", SIAM J.
+// Sci. Comput. 42, 2020). The products of FAB_B consecutive rows are summed in FP32 by
+// plain FMAs, and each block sum is added to a pair (s, c) by Knuth's TwoSum, so the error
+// bound is about FAB_B units of FP32 rounding whatever the length of the run (plain FP32
+// accumulation grows with it), for ~1.75 FP32 operations per product. The _rn intrinsics
+// keep the compiler from fusing or reordering the TwoSum steps. The pair is added to the
+// FP64 state as s + c.
+constexpr int FAB_B = 8;
+struct CompSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = __fadd_rn(s, x);
+    const float z = __fsub_rn(t, s);
+    c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z)));
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return f2d_exact(s) + f2d_exact(c); }
+};
+
+// An FP64 a-priori error D as two FP32 words (D ~ hi + lo to ~48 bits; hi truncated, the
+// remainder D - hi is exact in FP64), so that gamma D enters the FP32 sums as two products.
+__device__ __forceinline__ void split_d(double d, float& hi, float& lo) {
+  hi = d2f_rz(d);
+  lo = d2f_rz(d - f2d_exact(hi));
+}
+
 // Short runs: one thread per entry of P (and of u), dealt round robin over the workers,
 // up to EMAX entries per thread per pass; the gamma rows of the run (and their D) are
 // staged in shared memory in row chunks. Ranks whose gamma rows do not fit the pool read
-// G from L2 directly.
+// G from L2 directly. F32 (mixed mode): the gammas are FP32 values held in FP64 (exact
+// conversions) and every entry is a compensated FP32 sum (FABsum).
 template <class Team, bool F32>
 __device__ void acc_rows(const Team& T, const StreamDev& S, const double* Gsrc, const double* Dsrc, int a,
                          int len, int r, int w_lo) {
@@ -575,12 +604,18 @@ __device__ void acc_rows(const Team& T, const StreamDev& S, const double* Gsrc, 
   const long long nP = (long long)r * r, ntot = nP + r;
   constexpr int EMAX = 4;
   constexpr int POOL_V = POOL_DOUBLES * (int)(sizeof(double) / sizeof(V));
-  const bool staged = (r + 1) <= (POOL_V - 64);
+  constexpr int DW = F32 ? 2 : 1;  // words per staged D (hi, lo in mixed mode)
+  const bool staged = (r + DW) <= (POOL_V - 64);
   V* Gs = reinterpret_cast<V*>(smem_pool());
-  const int rows_per = staged ? max(1, min(len, (POOL_V - 64) / (r + 1))) : 1;
-  V* Ds = Gs + (size_t)rows_per * r;
+  const int rows_per = staged ? max(1, min(len, (POOL_V - 64) / (r + DW))) : 1;
+  V* Ds = Gs + (size_t)rows_per * r;  // D (FP64 mode) or D hi at [jj], D lo at [rows_per + jj]
+  auto gload = [&](const double* p) -> V {
+    if constexpr (F32) return d2f_rz(__ldcg(p));  // exact: the value is an FP32 number
+    else return __ldcg(p);
+  };
   for (long long base = 0; base < ntot; base += (long long)EMAX * tstride) {
     V acc[EMAX];
+    CompSum cs[F32 ? EMAX : 1];
     double old[EMAX];  // current P / u entries, loaded before the products
 #pragma unroll
     for (int q = 0; q < EMAX; ++q) acc[q] = V(0);
@@ -603,9 +638,12 @@ __device__ void acc_rows(const Team& T, const StreamDev& S, const double* Gsrc, 
 #pragma unroll 8
         for (int e = threadIdx.x; e < nr * r; e += NT) {
           const int jj = e / r, i = e - jj * r;
-          Gs[e] = (V)__ldcg(Gsrc + (size_t)(jb + jj) * rm + i);
+          Gs[e] = gload(Gsrc + (size_t)(jb + jj) * rm + i);
         }
-        for (int e = threadIdx.x; e < nr; e += NT) Ds[e] = (V)__ldcg(Dsrc + jb + e);
+        for (int e = threadIdx.x; e < nr; e += NT) {
+          if constexpr (F32) split_d(__ldcg(Dsrc + jb + e), Ds[e], Ds[rows_per + e]);
+          else Ds[e] = __ldcg(Dsrc + jb + e);
+        }
         __syncthreads();
       }
 #pragma unroll
@@ -615,38 +653,65 @@ __device__ void acc_rows(const Team& T, const StreamDev& S, const double* Gsrc, 
         const bool isP = e < nP;
         const int i = isP ? (int)(e / r) : (int)(e - nP);
         const int l = isP ? (int)(e - (long long)i * r) : 0;
-        V x0 = V(0), x1 = V(0), x2 = V(0), x3 = V(0);  // four independent chains
-        auto gterm = [&](int jj) -> V {
-          V gi, gl;
-          if (staged) {
-            gi = Gs[jj * r + i];
-            gl = isP ? Gs[jj * r + l] : Ds[jj];
-          } else {
-            gi = (V)__ldcg(Gsrc + (size_t)(jb + jj) * rm + i);
-            gl = (V)(isP ? __ldcg(Gsrc + (size_t)(jb + jj) * rm + l) : __ldcg(Dsrc + jb + jj));
+        auto gi_of = [&](int jj) -> V { return staged ? Gs[jj * r + i] : gload(Gsrc + (size_t)(jb + jj) * rm + i); };
+        auto gl_of = [&](int jj) -> V { return staged ? Gs[jj * r + l] : gload(Gsrc + (size_t)(jb + jj) * rm + l); };
+        if constexpr (F32) {
+          // FABsum: FP32 blocks of FAB_B rows (two independent FMA chains), each block
+          // sum added to the compensated pair
+          auto term = [&](float acc, int jj) -> float {
+            const float gi = gi_of(jj);
+            if (isP) return fmaf(gi, gl_of(jj), acc);
+            float dh, dl;
+            if (staged) {
+              dh = Ds[jj];
+              dl = Ds[rows_per + jj];
+            } else {
+              split_d(__ldcg(Dsrc + jb + jj), dh, dl);
+            }
+            return fmaf(gi, dh, fmaf(gi, dl, acc));
+          };
+          for (int j1 = 0; j1 < nr; j1 += FAB_B) {
+            const int j2 = min(nr, j1 + FAB_B);
+            float x0 = 0.f, x1 = 0.f;
+            int jj = j1;
+            for (; jj + 1 < j2; jj += 2) {
+              x0 = term(x0, jj);
+              x1 = term(x1, jj + 1);
+            }
+            if (jj < j2) x0 = term(x0, jj);
+            cs[q].add(x0 + x1);
           }
-          return gi * gl;
-        };
-        int jj = 0;
-        for (; jj + 3 < nr; jj += 4) {
-          x0 += gterm(jj);
-          x1 += gterm(jj + 1);
-          x2 += gterm(jj + 2);
-          x3 += gterm(jj + 3);
+        } else {
+          auto gterm = [&](int jj) -> V {
+            const V gi = gi_of(jj);
+            const V gl = isP ? gl_of(jj) : (staged ? Ds[jj] : __ldcg(Dsrc + jb + jj));
+            return gi * gl;
+          };
+          V x0 = V(0), x1 = V(0), x2 = V(0), x3 = V(0);  // four independent chains
+          int jj = 0;
+          for (; jj + 3 < nr; jj += 4) {
+            x0 += gterm(jj);
+            x1 += gterm(jj + 1);
+            x2 += gterm(jj + 2);
+            x3 += gterm(jj + 3);
+          }
+          for (; jj < nr; ++jj) x0 += gterm(jj);
+          acc[q] += (x0 + x1) + (x2 + x3);
         }
-        for (; jj < nr; ++jj) x0 += gterm(jj);
-        acc[q] += (x0 + x1) + (x2 + x3);
       }
     }
 #pragma unroll
     for (int q = 0; q < EMAX; ++q) {
       const long long e = e0 + (long long)q * tstride;
       if (e >= ntot) continue;
+      double add;
+      if constexpr (F32) add = cs[q].value();
+      else add = (double)acc[q];
       if (e < nP) {
         const int i = (int)(e / r), l = (int)(e - (long long)i * r);
-        S.P[(size_t)i * rm + l] = old[q] + (double)acc[q];
+        S.P[(size_t)i * rm + l] = old[q] + add;
       } else {
-        S.u[e - nP] = old[q] + (double)acc[q];
+        S.u[e - nP] = old[q] + add;
       }
     }
   }
@@ -654,17 +719,23 @@ __device__ void acc_rows(const Team& T, const StreamDev& S, const double* Gsrc, 
 
 // Long runs, step 1: partial Gram sums per chunk of rows; CTA item = (16 x 16 tile pair
 // with ti <= tl, chunk). Diagonal tiles also accumulate sum_j gamma_j D_j for their rows.
+// F32 (mixed mode): compensated FP32 sums (FABsum; D as an FP32 hi/lo pair).
 template <class Team, bool F32>
 __device__ void gram_partials(const Team& T, const StreamDev& S, int a, int len, int r, int nch) {
   using V = typename std::conditional<F32, float, double>::type;
   V(*gi_s)[17] = reinterpret_cast<V(*)[17]>(smem_pool());
   V(*gl_s)[17] = gi_s + 32;
   V* d_s = reinterpret_cast<V*>(gl_s + 32);
+  V* dl_s = d_s + 32;  // D lo (mixed mode)
   const int rm = S.r_max;
   const int nt = (r + 15) / 16;
   const int npairs = nt * (nt + 1) / 2;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int per = (len + nch - 1) / nch;
+  auto gload = [&](const double* p) -> V {
+    if constexpr (F32) return d2f_rz(__ldcg(p));  // exact: the value is an FP32 number
+    else return __ldcg(p);
+  };
   for (int it = T.id(); it < npairs * nch; it += T.size()) {
     const int c = it / npairs;
     int pr = it - c * npairs, ti = 0;
@@ -675,27 +746,66 @@ __device__ void gram_partials(const Team& T, const StreamDev& S, int a, int len,
     const int tl = ti + pr;
     const int jlo = a + c * per, jhi = min(a + len, jlo + per);
     V acc = V(0), uacc = V(0);
+    CompSum pc, uc;
     for (int jb = jlo; jb < jhi; jb += 32) {
       __syncthreads();
 #pragma unroll 2
       for (int e = threadIdx.x; e < 32 * 16; e += NT) {
         const int jj = e >> 4, cc = e & 15;
         const int j = jb + jj, i = ti * 16 + cc, l = tl * 16 + cc;
-        gi_s[jj][cc] = (j < jhi && i < r) ? (V)__ldcg(S.G + (size_t)j * rm + i) : V(0);
-        gl_s[jj][cc] = (j < jhi && l < r) ? (V)__ldcg(S.G + (size_t)j * rm + l) : V(0);
+        gi_s[jj][cc] = (j < jhi && i < r) ? gload(S.G + (size_t)j * rm + i) : V(0);
+        gl_s[jj][cc] = (j < jhi && l < r) ? gload(S.G + (size_t)j * rm + l) : V(0);
       }
-      if (threadIdx.x < 32) d_s[threadIdx.x] = (jb + threadIdx.x < jhi) ? (V)__ldcg(S.Dall + jb + threadIdx.x) : V(0);
+      if (threadIdx.x < 32) {
+        const bool ok = jb + threadIdx.x < jhi;
+        if constexpr (F32) {
+          float h = 0.f, l = 0.f;
+          if (ok) split_d(__ldcg(S.Dall + jb + threadIdx.x), h, l);
+          d_s[threadIdx.x] = h;
+          dl_s[threadIdx.x] = l;
+        } else {
+          d_s[threadIdx.x] = ok ? __ldcg(S.Dall + jb + threadIdx.x) : V(0);
+        }
+      }
       __syncthreads();
+      if constexpr (F32) {  // FABsum: FP32 blocks of FAB_B rows, compensated block sums
+#pragma unroll
+        for (int j1 = 0; j1 < 32; j1 += FAB_B) {
+          float x0 = 0.f, x1 = 0.f;
+#pragma unroll
+          for (int jj = j1; jj < j1 + FAB_B; jj += 2) {
+            x0 = fmaf(gi_s[jj][ty], gl_s[jj][tx], x0);
+            x1 = fmaf(gi_s[jj + 1][ty], gl_s[jj + 1][tx], x1);
+          }
+          pc.add(x0 + x1);
+          if (tx == 0) {
+            float y0 = 0.f;
+#pragma unroll
+            for (int jj = j1; jj < j1 + FAB_B; ++jj)
+              y0 = fmaf(gi_s[jj][ty], d_s[jj], fmaf(gi_s[jj][ty], dl_s[jj], y0));
+            uc.add(y0);
+          }
+        }
+      } else {
 #pragma unroll 8
-      for (int jj = 0; jj < 32; ++jj) {
-        acc = fma(gi_s[jj][ty], gl_s[jj][tx], acc);
-        if (tx == 0) uacc = fma(gi_s[jj][ty], d_s[jj], uacc);
+        for (int jj = 0; jj < 32; ++jj) {
+          acc = fma(gi_s[jj][ty], gl_s[jj][tx], acc);
+          if (tx == 0) uacc = fma(gi_s[jj][ty], d_s[jj], uacc);
+        }
       }
     }
     const int i = ti * 16 + ty, l = tl * 16 + tx;
     double* Pc = S.Pp + (size_t)c * r * r;
-    if (i < r && l < r) Pc[(size_t)i * r + l] = (double)acc;
-    if (ti == tl && tx == 0 && i < r) S.up[(size_t)c * rm + i] = (double)uacc;
+    double pv, uv;
+    if constexpr (F32) {
+      pv = pc.value();
+      uv = uc.value();
+    } else {
+      pv = acc;
+      uv = uacc;
+    }
+    if (i < r && l < r) Pc[(size_t)i * r + l] = pv;
+    if (ti == tl && tx == 0 && i < r) S.up[(size_t)c * rm + i] = uv;
   }
 }
 
@@ -730,8 +840,8 @@ __device__ __forceinline__ void acc_small(const Team& T, const StreamDev& S, int
 
 // A run of dependent rows [a, a + len): short runs directly, long runs through chunked
 // partial sums. Returns false if a team barrier gave up. The caller syncs afterwards.
-// F32 (mixed mode): the per-chunk sums of gamma gamma^T and gamma D are FP32 (the gammas
-// are FP32 projections), added to the FP64 P and u.
+// F32 (mixed mode): the per-chunk sums of gamma gamma^T and gamma D are compensated FP32
+// sums (FABsum) of the FP32 projections, added to the FP64 P and u.
 template <class Team, bool F32>
 __device__ bool dep_run(const Team& T, const StreamDev& S, int a, int len, int r) {
   if (len <= 0 || r == 0) return true;
@@ -770,12 +880,12 @@ __device__ bool dep_run(const Team& T, const StreamDev& S, int a, int len, int r
 // Publishes {applied, r_new, n_ind} in CTRL_APPLIED / CTRL_RNEW / CTRL_NIND; the caller
 // reads them after its next team barrier. Returns false if a bounded wait gave up.
 // =======================================================================================
-__device__ __forceinline__ bool sub_barrier(int* ctrl, int n, unsigned long long& target) {
+__device__ __forceinline__ bool sub_barrier(int* ctrl, int sub_off, int n, unsigned long long& target) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ctrl + CTRL_SUB_COUNT);
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ctrl + sub_off);
     target += (unsigned long long)n;
     red_release_add_u64(cnt, 1ull);
     if (ld_acquire_u64(cnt) < target) {
@@ -811,7 +921,7 @@ __device__ __forceinline__ bool scan_exchange(const Team& T, const StreamDev& S,
   if (nact > 1) {
     double* Sp = S.Sp + (size_t)parity * S.sp_stride;
     if (threadIdx.x < 32) Sp[(size_t)T.id() * 32 + threadIdx.x] = a;
-    if (!sub_barrier(S.ctrl, nact, bar_target)) return false;
+    if (!sub_barrier(S.ctrl, S.sub_off, nact, bar_target)) return false;
     if (threadIdx.x < 32) {
       a = 0.0;
       for (int w2 = 0; w2 < nact; ++w2) a += __ldcg(Sp + (size_t)w2 * 32 + threadIdx.x);
@@ -822,9 +932,15 @@ __device__ __forceinline__ bool scan_exchange(const Team& T, const StreamDev& S,
   return true;
 }
 
-template <class Team, bool ORTHO>
+template <class Team, int VAR>
 __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, long long j0, int q0,
                           int bend, int r) {
+  constexpr bool ORTHO = VAR == VAR_ORTHONORMAL;
+  // the new basis row kept in Kv: general K = Gamma_r / s (the new dual row), orthonormal
+  // Gamma_r / sqrt(s), orthogonal Gamma_r itself
+  auto kv_scale = [](double is, double rsq) -> double {
+    return VAR == VAR_ORTHONORMAL ? rsq : (VAR == VAR_ORTHOGONAL ? 1.0 : is);
+  };
   const int m = S.m, ld = S.ld, rm = S.r_max;
   const int nrow = bend - q0;
   // grid teams: one warp per CTA owns 32 columns (registers), so that the FP64 work of a
@@ -851,7 +967,7 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
     }
     __shared__ unsigned long long bar_target_s;
     if (tid == 0 && nact > 1) {
-      const unsigned long long c = ld_acquire_u64(reinterpret_cast<unsigned long long*>(S.ctrl + CTRL_SUB_COUNT));
+      const unsigned long long c = ld_acquire_u64(reinterpret_cast<unsigned long long*>(S.ctrl + S.sub_off));
       bar_target_s = (c / (unsigned long long)nact) * (unsigned long long)nact;
     }
     __syncthreads();
@@ -879,7 +995,7 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
               S.jind[nind] = j;
               S.alpha[nind] = rsq;
               S.basis_rows[rc] = base_row + j;
-              S.wb[rc] = ORTHO ? 0.0 : yv;  // w_b <- [w_b; y] (general) or [w_b; 0] (orthonormal)
+              S.wb[rc] = VAR == VAR_GENERAL ? yv : 0.0;  // w_b <- [w_b; y] (general), [w_b; 0] (Section 2.2)
             }
           }
         }
@@ -929,7 +1045,7 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
           else tot[tid] = pv;
         }
         if (nact > 1) {
-          if (!sub_barrier(S.ctrl, nact, bar_target)) return false;
+          if (!sub_barrier(S.ctrl, S.sub_off, nact, bar_target)) return false;
           // value k = lane, summed over the owners w = warp, warp + NWARP, ... (a fixed
           // pairwise tree, all loads issued first: up to 20 owners per warp), then over
           // the warps; every CTA sums in the same order
@@ -961,7 +1077,7 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
         }
         if (d == 1) {
           const double is = is_s;
-          const double scale = ORTHO ? rsq_s : is;
+          const double scale = kv_scale(is, rsq_s);
           if (warp == 0 && colv) S.Kv[(size_t)nind * ld + c] = rj * scale;
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -1010,7 +1126,7 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
         }
         if (d == 1) {
           const double is = is_s;
-          const double scale = ORTHO ? rsq_s : is;
+          const double scale = kv_scale(is, rsq_s);
           for (long long c = col0; c < m; c += cstride) {
             const double rj = rload(Rb + (size_t)jj * ldr + c);
             S.Kv[(size_t)nind * ld + c] = rj * scale;
@@ -1052,9 +1168,9 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
             for (int t2 = tt + 1; t2 < 32; ++t2) {
               if (t2 < napp) {
                 const double kap = kap_s[q * SLOW_MAX + t2];
-                if (i < rcv) {
-                  if (!ORTHO) g[t2] = fma(-kap, g[tt], g[t2]);
-                } else if (i == rcv) {
+                if (i < rcv) {  // general: the raw row also has components on the old basis
+                  if (VAR == VAR_GENERAL) g[t2] = fma(-kap, g[tt], g[t2]);
+                } else if (i == rcv) {  // coordinate on the new basis row
                   g[t2] = ORTHO ? kap * sq : kap;
                 }
               }
@@ -1089,9 +1205,10 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
 // Apply the sequential section's rows [q0, q0 + napp) to P and u (team-wide, one thread
 // per entry of the new r_new x r_new P and of u). Rows are taken in order with the rank
 // r_j each saw: a dependent row adds gamma_j gamma_j^T on the leading r_j x r_j block and
-// gamma_j D_j to u; an independent row opens entry r_j (general: P_jj = 1; orthonormal:
-// adds g g^T with g = [gamma_j; 1/alpha_j] and g D_j to u).
-template <class Team, bool ORTHO>
+// gamma_j D_j to u; an independent row opens entry r_j (general: P_jj = 1; orthonormal and
+// orthogonal: adds g g^T with g = [gamma_j; 1/alpha_j] and g D_j to u, alpha_j = 1 for the
+// orthogonal variant).
+template <class Team, int VAR>
 __device__ void section_apply_pu(const Team& T, const StreamDev& S, int q0, int napp, int r,
                                  int rnew) {
   const int rm = S.r_max;
@@ -1114,8 +1231,8 @@ __device__ void section_apply_pu(const Team& T, const StreamDev& S, int q0, int 
           acc = fma(__ldcg(g + i), __ldcg(S.Dall + j), acc);
         }
       } else {  // independent: opens entry rj
-        if (ORTHO) {
-          const double ia = 1.0 / __ldcg(S.alpha + q);
+        if (VAR != VAR_GENERAL) {  // g = [gamma_j; 1/alpha_j], alpha = 1 (orthogonal)
+          const double ia = VAR == VAR_ORTHONORMAL ? 1.0 / __ldcg(S.alpha + q) : 1.0;
           const double gi = (i < rj) ? __ldcg(S.Gind + (size_t)q * rm + i) : (i == rj ? ia : 0.0);
           if (isP) {
             const double gl = (l < rj) ? __ldcg(S.Gind + (size_t)q * rm + l) : (l == rj ? ia : 0.0);
@@ -1142,17 +1259,29 @@ __device__ void section_apply_pu(const Team& T, const StreamDev& S, int q0, int 
 }
 
 // Appends of the sequential section to the basis, team-wide.
+// Orthogonal variant: C[r + q] = Gamma_r,q and Ct[r + q] = Gamma_r,q / ||Gamma_r,q||^2.
 // General variant: Ct_final[i] = base_i - sum_{q >= qmin(i)} Gind[q][i] K_q with
 // base_i = Ct[i] (i < r) or K_{i-r}, qmin(i) = max(0, i - r + 1); C[r + q] = Gamma_{jind[q]}.
 // Orthonormal variant: Q[r + q] = alpha_q Gamma_r (already scaled in Kv) and, with FP32
 // projections, its FP32 copy.
-template <class Team, bool ORTHO>
+template <class Team, int VAR>
 __device__ void section_apply_basis(const Team& T, const StreamDev& S, const CallArgs& A, long long j0,
                                     int r, int nind) {
   const int m = S.m, ld = S.ld, rm = S.r_max;
   const long long gt = (long long)T.id() * NT + threadIdx.x;
   const long long tstride = (long long)T.size() * NT;
-  if (ORTHO) {
+  if (VAR == VAR_ORTHOGONAL) {  // C[r + q] = Gamma_r (in Kv), Ct[r + q] = Gamma_r / s; old rows kept
+    const long long n = (long long)nind * m;
+    for (long long e = gt; e < n; e += tstride) {
+      const int q = (int)(e / m), c = (int)(e - (long long)q * m);
+      const double v = __ldcg(S.Kv + (size_t)q * ld + c);
+      const double a = __ldcg(S.alpha + q);  // 1 / sqrt(s)
+      S.C[(size_t)(r + q) * ld + c] = v;
+      S.Ct[(size_t)(r + q) * ld + c] = v * a * a;
+    }
+    return;
+  }
+  if (VAR == VAR_ORTHONORMAL) {
     const long long n = (long long)nind * m;
     for (long long e = gt; e < n; e += tstride) {
       const int q = (int)(e / m), c = (int)(e - (long long)q * m);
@@ -1191,8 +1320,67 @@ __device__ void section_apply_basis(const Team& T, const StreamDev& S, const Cal
 //  * otherwise: worker 0 decides; the dependent run before the first special row is
 //    accumulated; from that row the sequential FP64 section applies the rank changes.
 // =======================================================================================
-template <class Team, bool F32, bool ORTHO = F32>
+// Steps 4 and 5 of a block whose rows [0, b) (call rows j0 + [0, b)) have their gamma in
+// S.G, their norms in S.s / S.t and their a-priori errors in S.Dall, and whose first row
+// that needs the sequential section is q0 (b if none): the dependent run before q0, the
+// FP64 section from q0 (rank tests in order, appends, fix-ups of the later rows), and the
+// block's bookkeeping (flags, counters, rank, next block size), followed by a team barrier.
+// Returns the rows applied, or -1 if a bounded team barrier gave up.
+template <class Team, bool F32, int VAR>
+__device__ int block_tail(const Team& T, const StreamDev& S, const CallArgs& A, long long j0, int b,
+                          int r, int q0, int kb0) {
+  constexpr bool ORTHO = VAR == VAR_ORTHONORMAL;  // the projection basis is C itself
+  __shared__ int shc[3];
+  const double* gam = A.Gamma + (size_t)j0 * S.m;
+  // 4: dependent run before the first special row
+  if (q0 > 0 && !dep_run<Team, F32>(T, S, 0, q0, r)) return -1;
+  int applied = b, rnew = r;
+  if (q0 < b) {
+    // 5: sequential section, in FP64 (rows [q0, bend)); its rows never overlap the run
+    const int bend = min(b, q0 + SLOW_MAX);
+    if ((long long)((bend - q0 + 7) / 8) * r < 4LL * NWARP * T.size())
+      phase_gamma_cta(T, S, gam, q0, bend, r, ORTHO ? S.C : S.Ct);
+    else
+      phase_gamma<Team, false>(T, S, gam, q0, bend, r, ORTHO ? S.C : S.Ct);
+    if (!T.sync()) return -1;
+    phase_reject<Team, false, 1>(T, S, gam, q0, bend, r, S.C, S.R);
+    if (!T.sync()) return -1;
+    if (!scan_team<Team, VAR>(T, S, A, j0, q0, bend, r)) return -1;
+    // the scan may have used the dynamic shared memory that caches the tensor-core B tiles
+    if (S.tcx && threadIdx.x == 0) reinterpret_cast<TcCtx*>(S.tcx)->cq = nullptr;
+    if (!T.sync()) return -1;
+    if (threadIdx.x == 0) {
+      shc[0] = __ldcg(S.ctrl + CTRL_APPLIED);  // published before the barrier above
+      shc[1] = __ldcg(S.ctrl + CTRL_RNEW);
+      shc[2] = __ldcg(S.ctrl + CTRL_NIND);
+    }
+    __syncthreads();
+    applied = shc[0];
+    rnew = shc[1];
+    const int nind = shc[2];
+    section_apply_pu<Team, VAR>(T, S, q0, applied - q0, r, rnew);
+    if (nind > 0) section_apply_basis<Team, VAR>(T, S, A, j0, r, nind);
+  }
+  // finalize the block (worker 0): flags, counters, rank, next block size
+  if (T.id() == 0) {
+    if (A.indep)
+      for (int j = threadIdx.x; j < applied; j += NT)
+        A.indep[j0 + j] = (j < q0) ? 0 : (uint8_t)(__ldcg(S.rowflag + j) - 1);
+    if (threadIdx.x == 0) {
+      *S.rows_seen = __ldcg(S.rows_seen) + applied;
+      S.ctrl[CTRL_R] = rnew;
+      S.ctrl[CTRL_KB] = (q0 < b) ? min(KB_MIN, S.kb_max) : min(2 * kb0, S.kb_max);
+      S.ctrl[CTRL_PEND] = 1;
+      S.ctrl[CTRL_PEND_ROWS] = 0;
+    }
+  }
+  if (!T.sync()) return -1;
+  return applied;
+}
+
+template <class Team, bool F32, int VAR = (F32 ? VAR_ORTHONORMAL : VAR_GENERAL)>
 __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& A) {
+  constexpr bool ORTHO = VAR == VAR_ORTHONORMAL;  // the projection basis is C itself
   __shared__ int sh[8];
   long long j0 = 0;
   while (j0 < A.k) {
@@ -1274,49 +1462,8 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
         q0 = sh[3];
       }
     }
-    // 4: dependent run before the first special row
-    if (q0 > 0 && !dep_run<Team, F32>(T, S, 0, q0, r)) return false;
-    int applied = b, rnew = r;
-    if (q0 < b) {
-      // 5: sequential section, in FP64 (rows [q0, bend)); its rows never overlap the run
-      const int bend = min(b, q0 + SLOW_MAX);
-      if ((long long)((bend - q0 + 7) / 8) * r < 4LL * NWARP * T.size())
-        phase_gamma_cta(T, S, gam, q0, bend, r, ORTHO ? S.C : S.Ct);
-      else
-        phase_gamma<Team, false>(T, S, gam, q0, bend, r, ORTHO ? S.C : S.Ct);
-      if (!T.sync()) return false;
-      phase_reject<Team, false, 1>(T, S, gam, q0, bend, r, S.C, S.R);
-      if (!T.sync()) return false;
-      if (!scan_team<Team, ORTHO>(T, S, A, j0, q0, bend, r)) return false;
-      // the scan may have used the dynamic shared memory that caches the tensor-core B tiles
-      if (S.tcx && threadIdx.x == 0) reinterpret_cast<TcCtx*>(S.tcx)->cq = nullptr;
-      if (!T.sync()) return false;
-      if (threadIdx.x == 0) {
-        sh[5] = __ldcg(S.ctrl + CTRL_APPLIED);  // published before the barrier above
-        sh[6] = __ldcg(S.ctrl + CTRL_RNEW);
-        sh[7] = __ldcg(S.ctrl + CTRL_NIND);
-      }
-      __syncthreads();
-      applied = sh[5];
-      rnew = sh[6];
-      const int nind = sh[7];
-      section_apply_pu<Team, ORTHO>(T, S, q0, applied - q0, r, rnew);
-      if (nind > 0) section_apply_basis<Team, ORTHO>(T, S, A, j0, r, nind);
-    }
-    // finalize the block (worker 0): flags, counters, rank, next block size
-    if (T.id() == 0) {
-      if (A.indep)
-        for (int j = threadIdx.x; j < applied; j += NT)
-          A.indep[j0 + j] = (j < q0) ? 0 : (uint8_t)(__ldcg(S.rowflag + j) - 1);
-      if (threadIdx.x == 0) {
-        *S.rows_seen = __ldcg(S.rows_seen) + applied;
-        S.ctrl[CTRL_R] = rnew;
-        S.ctrl[CTRL_KB] = (q0 < b) ? min(KB_MIN, S.kb_max) : min(2 * kb0, S.kb_max);
-        S.ctrl[CTRL_PEND] = 1;
-        S.ctrl[CTRL_PEND_ROWS] = 0;
-      }
-    }
-    if (!T.sync()) return false;
+    const int applied = block_tail<Team, F32, VAR>(T, S, A, j0, b, r, q0, kb0);
+    if (applied < 0) return false;
     j0 += applied;
   }
   return true;

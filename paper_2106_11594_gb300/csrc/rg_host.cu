@@ -211,7 +211,10 @@ rg_status rg_init(rg_state** out, int64_t m, double tol, int flags, int64_t r_ma
   *out = nullptr;
   if (m <= 0 || m > (1 << 24)) return fail(RG_EINVAL, "rg_init: m = %lld out of range", (long long)m);
   if (std::isnan(tol)) return fail(RG_EINVAL, "rg_init: tol is NaN");
-  if (flags & ~(RG_MIXED | RG_TEST_PAPER | RG_ORTHONORMAL)) return fail(RG_EINVAL, "rg_init: unknown flags %d", flags);
+  if (flags & ~(RG_MIXED | RG_TEST_PAPER | RG_ORTHONORMAL | RG_ORTHOGONAL))
+    return fail(RG_EINVAL, "rg_init: unknown flags %d", flags);
+  if ((flags & RG_ORTHOGONAL) && (flags & (RG_MIXED | RG_ORTHONORMAL)))
+    return fail(RG_EINVAL, "rg_init: RG_ORTHOGONAL excludes RG_MIXED and RG_ORTHONORMAL");
   if (r_max <= 0 || r_max > m) r_max = m;
   rg_state* st = new (std::nothrow) rg_state();
   if (!st) return fail(RG_ENOMEM, "rg_init: host allocation failed");
@@ -227,6 +230,7 @@ rg_status rg_init(rg_state** out, int64_t m, double tol, int flags, int64_t r_ma
   S.r_max = (int)r_max;
   S.mixed = (flags & RG_MIXED) ? 1 : 0;
   S.ortho = (flags & (RG_MIXED | RG_ORTHONORMAL)) ? 1 : 0;
+  S.orthog = (flags & RG_ORTHOGONAL) ? 1 : 0;
   S.test_mode = (flags & RG_TEST_PAPER) ? 2 : 0;
   S.tol = tol;
   S.tau_lo = 1e-5;
@@ -246,7 +250,7 @@ rg_status rg_init(rg_state** out, int64_t m, double tol, int flags, int64_t r_ma
     return cuda_fail(e, "rg_init: cudaMalloc of the state");
   }
   carve(S, (char*)st->arena, st->Gs, st->Ds);
-  e = stream_grid_size(S.mixed, S.ortho, &st->grid);
+  e = stream_grid_size(S.mixed, S.ortho, S.orthog, &st->grid);
   if (e != cudaSuccess || st->grid <= 0) {
     cudaFree(st->arena);
     delete st;
@@ -269,6 +273,7 @@ rg_status rg_init(rg_state** out, int64_t m, double tol, int flags, int64_t r_ma
 
 rg_status rg_add_rows(rg_state* st, const double* Gamma, const double* y, int64_t k,
                       uint8_t* indep_out) {
+  NvtxRange nvtx_range("rg_add_rows");
   if (!valid_state(st)) return fail(RG_EINVAL, "rg_add_rows: invalid state");
   if (k < 0) return fail(RG_EINVAL, "rg_add_rows: k = %lld < 0", (long long)k);
   if (k == 0) return RG_OK;
@@ -282,6 +287,7 @@ rg_status rg_add_rows(rg_state* st, const double* Gamma, const double* y, int64_
 
 rg_status rg_add_rows_host(rg_state* st, const double* Gamma, const double* y, int64_t k,
                            uint8_t* indep_out) {
+  NvtxRange nvtx_range("rg_add_rows_host");
   if (!valid_state(st)) return fail(RG_EINVAL, "rg_add_rows_host: invalid state");
   if (k < 0) return fail(RG_EINVAL, "rg_add_rows_host: k = %lld < 0", (long long)k);
   if (k == 0) return RG_OK;
@@ -342,6 +348,7 @@ rg_status rg_add_rows_host(rg_state* st, const double* Gamma, const double* y, i
 }
 
 rg_status rg_solution(rg_state* st, double* X, int64_t* rank_out) {
+  NvtxRange nvtx_range("rg_solution");
   if (!valid_state(st)) return fail(RG_EINVAL, "rg_solution: invalid state");
   if (!X) return fail(RG_EINVAL, "rg_solution: X is NULL");
   cudaError_t e = launch_flush(flush_view(st), st->grid, st->stream);
@@ -353,6 +360,7 @@ rg_status rg_solution(rg_state* st, double* X, int64_t* rank_out) {
 
 rg_status rg_adjoint(rg_state* st, const double* A, const double* y, int64_t n, const double* g,
                      double* gA, double* gy, double* X) {
+  NvtxRange nvtx_range("rg_adjoint");
   if (!valid_state(st)) return fail(RG_EINVAL, "rg_adjoint: invalid state");
   if (n < 0) return fail(RG_EINVAL, "rg_adjoint: n = %lld < 0", (long long)n);
   if (!g || (n > 0 && (!A || !y || !gA || !gy)))
@@ -402,6 +410,7 @@ rg_status rg_adjoint(rg_state* st, const double* A, const double* y, int64_t n, 
 }
 
 rg_status rg_pinv(rg_state* st, const double* A, int64_t n, double* Apinv, int64_t ld) {
+  NvtxRange nvtx_range("rg_pinv");
   if (!valid_state(st)) return fail(RG_EINVAL, "rg_pinv: invalid state");
   if (n < 0) return fail(RG_EINVAL, "rg_pinv: n = %lld < 0", (long long)n);
   if (n > 0 && (!A || !Apinv)) return fail(RG_EINVAL, "rg_pinv: NULL buffer");
@@ -425,6 +434,7 @@ rg_status rg_pinv(rg_state* st, const double* A, int64_t n, double* Apinv, int64
 }
 
 rg_status rg_solution_host(rg_state* st, double* X, int64_t* rank_out) {
+  NvtxRange nvtx_range("rg_solution_host");
   if (!valid_state(st)) return fail(RG_EINVAL, "rg_solution_host: invalid state");
   if (!X) return fail(RG_EINVAL, "rg_solution_host: X is NULL");
   if (!st->xbuf) {
@@ -479,6 +489,7 @@ rg_status rg_reset(rg_state* st) {
 
 rg_status rg_export(rg_state* st, double* C, double* Ct, double* Pinv, double* w,
                     int64_t* basis_rows, int64_t capacity, int64_t* rank_out) {
+  NvtxRange nvtx_range("rg_export");
   if (!valid_state(st)) return fail(RG_EINVAL, "rg_export: invalid state");
   int64_t r = 0;
   rg_status s = rg_rank(st, &r);
@@ -492,6 +503,39 @@ rg_status rg_export(rg_state* st, double* C, double* Ct, double* Pinv, double* w
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
   if (e != cudaSuccess) return cuda_fail(e, "rg_export");
   if (rank_out) *rank_out = r;
+  return RG_OK;
+}
+
+rg_status rg_snapshot_size(rg_state* st, int64_t* bytes_out) {
+  if (!valid_state(st) || !bytes_out) return fail(RG_EINVAL, "rg_snapshot_size: invalid argument");
+  *bytes_out = (int64_t)snapshot_bytes(st->S);
+  return RG_OK;
+}
+
+rg_status rg_snapshot(rg_state* st, void* buf, int64_t bytes) {
+  NvtxRange nvtx_range("rg_snapshot");
+  if (!valid_state(st)) return fail(RG_EINVAL, "rg_snapshot: invalid state");
+  if (!buf) return fail(RG_EINVAL, "rg_snapshot: buf is NULL");
+  if ((uintptr_t)buf % 256) return fail(RG_EINVAL, "rg_snapshot: buf is not 256-byte aligned");
+  const size_t need = snapshot_bytes(st->S);
+  if (bytes < (int64_t)need)
+    return fail(RG_EINVAL, "rg_snapshot: %lld bytes given, %zu needed", (long long)bytes, need);
+  cudaError_t e = launch_flush(flush_view(st), st->grid, st->stream);
+  if (e == cudaSuccess) e = launch_snapshot(st->S, buf, st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_snapshot: launch");
+  return RG_OK;
+}
+
+rg_status rg_restore(rg_state* st, const void* buf, int64_t bytes) {
+  NvtxRange nvtx_range("rg_restore");
+  if (!valid_state(st)) return fail(RG_EINVAL, "rg_restore: invalid state");
+  if (!buf) return fail(RG_EINVAL, "rg_restore: buf is NULL");
+  if ((uintptr_t)buf % 256) return fail(RG_EINVAL, "rg_restore: buf is not 256-byte aligned");
+  const size_t need = snapshot_bytes(st->S);
+  if (bytes < (int64_t)need)
+    return fail(RG_EINVAL, "rg_restore: %lld bytes given, %zu needed", (long long)bytes, need);
+  cudaError_t e = launch_restore(st->S, buf, st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_restore: launch");
   return RG_OK;
 }
 

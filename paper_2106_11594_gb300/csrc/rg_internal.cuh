@@ -21,6 +21,12 @@ constexpr int GRAM_CHUNK = 128;  // rows per Gram-path chunk (at least)
 constexpr int GRAM_RMAX = 2048;  // the Gram path is used for ranks up to this
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // bounded waits: 2 s
 
+// Rank factorizations kept (template parameter VAR of the update): Algorithm 1's general
+// variant (C = selected rows, Ct its dual basis) and the two variants of Section 2.2 --
+// orthonormal (alpha = 1/||Gamma_r||: C = Q, its own dual) and orthogonal (alpha = 1:
+// C holds the raw rejections, Ct the same rows over their squared norms).
+enum : int { VAR_GENERAL = 0, VAR_ORTHONORMAL = 1, VAR_ORTHOGONAL = 2 };
+
 // Device status bits (mapped to rg_status on the host).
 enum : int { ST_NONFINITE = 1, ST_CAPACITY = 2, ST_TIMEOUT = 4, ST_BADARG = 8 };
 
@@ -38,7 +44,11 @@ enum : int {
   CTRL_PEND_ROWS = 11, // rows of the previous call whose P/u update was deferred (in Gpend)
   CTRL_SUB_COUNT = 32, // barrier counter of the sequential section's column owners (words
                        // 32-33, a cache line apart from the grid barrier's counter)
-  CTRL_N = 64
+  CTRL_SBAR_COUNT = 64,  // the same two counters for the cluster kernel of small calls, whose
+  CTRL_SSUB_COUNT = 96,  // grid has another size (each counter is a multiple of its grid's
+                         // size between launches); words 64-65 and 96-97, own cache lines
+  CTRL_SKEY = 80,      // small calls: 64-bit (call number, first special row) key (words 80-81)
+  CTRL_N = 128
 };
 
 // Everything a kernel needs to know about one stream. Plain pointers into device
@@ -51,8 +61,11 @@ enum : int {
 struct StreamDev {
   int m, ld, r_max, kb_max;
   int mixed;      // 1: FP32 projections (implies the orthonormal variant)
-  int ortho;      // 1: orthonormal variant
+  int ortho;      // 1: orthonormal variant (Ct is C itself)
+  int orthog;     // 1: orthogonal variant (C and Ct both kept, as in the general variant)
   int test_mode;  // 0 REL, 2 PAPER
+  int bar_off = CTRL_BAR_COUNT;  // control words of the grid barrier and of the section's
+  int sub_off = CTRL_SUB_COUNT;  // barrier used by this launch (see CTRL_SBAR_COUNT)
   double tol;     // <= 0: paper default (m^2 r + m r + m) eps_M
   double tau_lo;  // mixed mode: FP32 relative-rejection floor below which rows are dependent
   double* C;      // r_max x ld
@@ -77,7 +90,7 @@ struct StreamDev {
   double* R;      // SLOW_MAX x ld: FP64 rejections of the sequential section
   double* Kv;     // SLOW_MAX x ld: new dual rows K (general) or new Q rows (orthonormal)
   double* Gind;   // SLOW_MAX x r_max: gamma (fixed up) of each independent row
-  double* alpha;  // SLOW_MAX: orthonormal scale 1/||Gamma_r|| of each independent row
+  double* alpha;  // SLOW_MAX: 1/||Gamma_r|| of each independent row of the section
   int* jind;      // SLOW_MAX: block row of each independent row
   double* Dall;   // kb_max: a-priori errors y_j - gamma_j^T w_b of the block's rows
   double* Pp;     // pp_cap doubles: Gram partials, chunk c at Pp + c * r * r
@@ -172,12 +185,12 @@ __device__ __forceinline__ unsigned long long atom_release_add_u64(unsigned long
   asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
   return old;
 }
-__device__ __forceinline__ bool grid_barrier(int* ctrl) {
+__device__ __forceinline__ bool grid_barrier(int* ctrl, int bar_off = CTRL_BAR_COUNT) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ctrl + CTRL_BAR_COUNT);
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ctrl + bar_off);
     const unsigned long long old = atom_release_add_u64(cnt, 1ull);
     const unsigned long long target = (old / gridDim.x + 1) * gridDim.x;
     if (ld_acquire_u64(cnt) < target) {

@@ -85,16 +85,19 @@ size_t noalloc_layout(StreamDev& S, char* base) {
 
 }  // namespace
 
-template <bool F32, bool ORTHO>
+template <bool F32, int VAR>
 __global__ void __launch_bounds__(NT, 1) noalloc_kernel(StreamDev S, CallArgs A) {
   grid_barrier_init(S.ctrl);
-  process_rows<GridTeam, F32, ORTHO>(GridTeam{S.ctrl}, S, A);
+  process_rows<GridTeam, F32, VAR>(GridTeam{S.ctrl}, S, A);
 }
 
-// FP32 projections always come with the orthonormal variant.
-static const void* noalloc_kernel_ptr(int mixed, int ortho) {
-  if (mixed) return (const void*)noalloc_kernel<true, true>;
-  return ortho ? (const void*)noalloc_kernel<false, true> : (const void*)noalloc_kernel<false, false>;
+// FP32 projections always come with the orthonormal variant. v: 0 general, 1 orthonormal
+// (FP64), 2 mixed, 3 orthogonal.
+static const void* noalloc_kernel_ptr(int v) {
+  if (v == 2) return (const void*)noalloc_kernel<true, VAR_ORTHONORMAL>;
+  if (v == 1) return (const void*)noalloc_kernel<false, VAR_ORTHONORMAL>;
+  if (v == 3) return (const void*)noalloc_kernel<false, VAR_ORTHOGONAL>;
+  return (const void*)noalloc_kernel<false, VAR_GENERAL>;
 }
 
 // Clears what must start at zero before each call: the control words (rank, status,
@@ -127,12 +130,15 @@ using namespace rg;
 extern "C" rg_status rg_solve_noalloc(const double* Gamma, const double* y, int64_t n, int64_t m,
                                       double tol, int flags, int64_t r_max, double* X,
                                       int64_t* rank_out, void* cuda_stream) {
+  NvtxRange nvtx_range("rg_solve_noalloc");
   if (m <= 0 || m > (1 << 24)) return fail(RG_EINVAL, "rg_solve_noalloc: m = %lld out of range", (long long)m);
   if (n < 0) return fail(RG_EINVAL, "rg_solve_noalloc: n = %lld < 0", (long long)n);
   if ((n > 0 && (!Gamma || !y)) || !X) return fail(RG_EINVAL, "rg_solve_noalloc: NULL buffer");
   if (std::isnan(tol)) return fail(RG_EINVAL, "rg_solve_noalloc: tol is NaN");
-  if (flags & ~(RG_MIXED | RG_TEST_PAPER | RG_ORTHONORMAL))
+  if (flags & ~(RG_MIXED | RG_TEST_PAPER | RG_ORTHONORMAL | RG_ORTHOGONAL))
     return fail(RG_EINVAL, "rg_solve_noalloc: unknown flags %d", flags);
+  if ((flags & RG_ORTHOGONAL) && (flags & (RG_MIXED | RG_ORTHONORMAL)))
+    return fail(RG_EINVAL, "rg_solve_noalloc: RG_ORTHOGONAL excludes RG_MIXED and RG_ORTHONORMAL");
   if (r_max <= 0 || r_max > m) r_max = m;
   StreamDev S{};
   S.m = (int)m;
@@ -140,6 +146,7 @@ extern "C" rg_status rg_solve_noalloc(const double* Gamma, const double* y, int6
   S.r_max = (int)r_max;
   S.mixed = (flags & RG_MIXED) ? 1 : 0;
   S.ortho = (flags & (RG_MIXED | RG_ORTHONORMAL)) ? 1 : 0;
+  S.orthog = (flags & RG_ORTHOGONAL) ? 1 : 0;
   S.test_mode = (flags & RG_TEST_PAPER) ? 2 : 0;
   S.tol = tol;
   S.tau_lo = 1e-5;
@@ -169,12 +176,12 @@ extern "C" rg_status rg_solve_noalloc(const double* Gamma, const double* y, int6
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess) return cuda_fail(e, "rg_solve_noalloc: cudaGetSymbolAddress");
-      int nsm = 0, per[3] = {0, 0, 0};
+      int nsm = 0, per[4] = {0, 0, 0, 0};
       e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      for (int v = 0; v < 3 && e == cudaSuccess; ++v)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[v], noalloc_kernel_ptr(v == 2, v >= 1), NT, 0);
+      for (int v = 0; v < 4 && e == cudaSuccess; ++v)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[v], noalloc_kernel_ptr(v), NT, 0);
       if (e != cudaSuccess) return cuda_fail(e, "rg_solve_noalloc: occupancy query");
-      if (per[0] < 1 || per[1] < 1 || per[2] < 1)
+      if (per[0] < 1 || per[1] < 1 || per[2] < 1 || per[3] < 1)
         return fail(RG_ECUDA, "rg_solve_noalloc: kernel cannot be resident");
       g_noalloc_grid[dev] = std::min(nsm, 1024);
       g_noalloc_ptr[dev] = p;
@@ -190,7 +197,8 @@ extern "C" rg_status rg_solve_noalloc(const double* Gamma, const double* y, int6
   if (n > 0) {
     CallArgs A{Gamma, y, n, nullptr};
     void* args[] = {(void*)&S, (void*)&A};
-    e = cudaLaunchCooperativeKernel(noalloc_kernel_ptr(S.mixed, S.ortho), dim3(grid), dim3(NT), args, 0,
+    const int v = S.mixed ? 2 : (S.ortho ? 1 : (S.orthog ? 3 : 0));
+    e = cudaLaunchCooperativeKernel(noalloc_kernel_ptr(v), dim3(grid), dim3(NT), args, 0,
                                     stream);
     if (e != cudaSuccess) return cuda_fail(e, "rg_solve_noalloc: launch");
   }

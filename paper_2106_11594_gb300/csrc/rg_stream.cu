@@ -32,7 +32,8 @@
 // FP64 mode keeps the general factorization of Algorithm 1 (C = selected rows, Ct its dual
 // basis). Mixed mode keeps the orthonormal variant of Section 2.2 (alpha = 1/||Gamma_r||:
 // Ct = C = Q), projects in FP32 against an FP32 copy of Q, and re-decides every row whose
-// FP32 relative rejection exceeds the floor tau_lo in FP64.
+// FP32 relative rejection exceeds the floor tau_lo in FP64. FP64 mode can also keep either
+// variant of Section 2.2 (RG_ORTHONORMAL, RG_ORTHOGONAL).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,10 +43,10 @@
 
 namespace rg {
 
-template <bool F32, bool ORTHO>
+template <bool F32, int VAR>
 __global__ void __launch_bounds__(NT, 1) stream_kernel(StreamDev S, CallArgs A) {
   grid_barrier_init(S.ctrl);
-  process_rows<GridTeam, F32, ORTHO>(GridTeam{S.ctrl}, S, A);
+  process_rows<GridTeam, F32, VAR>(GridTeam{S.ctrl}, S, A);
 }
 
 // Folds the P/u update deferred by the last small call (if any) into P and u: every CTA
@@ -105,11 +106,163 @@ __global__ void export_kernel(StreamDev S, double* C, double* Ct, double* Pinv, 
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Snapshots of the factorization (checkpoint / resume, and gradients through intermediate
+// solutions): a header followed by the used rows of C, Ct (general variant), the FP32 copy
+// of Q (mixed mode), the leading r x r block of P, and w_b, u and the basis-row indices.
+// The buffer is laid out for r_max (its size is fixed at init); only rows below the rank,
+// read on the device, are copied.
+// ---------------------------------------------------------------------------------------
+constexpr unsigned SNAP_MAGIC = 0x52475331u;  // "RGS1"
+
+struct SnapHeader {
+  unsigned magic;
+  int m, ld, r_max, mixed, ortho, orthog;
+  int r, kb, pend;
+  long long rows_seen;
+};
+static_assert(sizeof(SnapHeader) <= 256, "snapshot header");
+
+struct SnapLayout {
+  size_t C, Ct, Qf, P, wb, u, basis, bytes;
+};
+
+__host__ __device__ inline SnapLayout snap_layout(int ld, int rm, int mixed, int ortho) {
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  SnapLayout L{};
+  size_t off = 256;
+  L.C = off;
+  off += al((size_t)rm * ld * 8);
+  L.Ct = ortho ? 0 : off;
+  if (!ortho) off += al((size_t)rm * ld * 8);
+  L.Qf = mixed ? off : 0;
+  if (mixed) off += al((size_t)rm * ld * 4);
+  L.P = off;
+  off += al((size_t)rm * rm * 8);
+  L.wb = off;
+  off += al((size_t)rm * 8);
+  L.u = off;
+  off += al((size_t)rm * 8);
+  L.basis = off;
+  off += al((size_t)rm * 8);
+  L.bytes = off;
+  return L;
+}
+
+size_t snapshot_bytes(const StreamDev& S) { return snap_layout(S.ld, S.r_max, S.mixed, S.ortho).bytes; }
+
+// Copies the state into buf (grid-stride; rows below the rank only). Runs after the
+// deferred P/u update has been folded (flush_pending_kernel), so it also clears the
+// pending count, as form_w_kernel does.
+__global__ void snapshot_kernel(StreamDev S, unsigned char* buf) {
+  const SnapLayout L = snap_layout(S.ld, S.r_max, S.mixed, S.ortho);
+  const int r = S.ctrl[CTRL_R];
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long str = (long long)gridDim.x * blockDim.x;
+  const long long nrow = (long long)r * S.ld;
+  double* C = reinterpret_cast<double*>(buf + L.C);
+  double* Ct = reinterpret_cast<double*>(buf + L.Ct);
+  float* Qf = reinterpret_cast<float*>(buf + L.Qf);
+  for (long long e = tid; e < nrow; e += str) {
+    C[e] = S.C[e];
+    if (!S.ortho) Ct[e] = S.Ct[e];
+    if (S.mixed) Qf[e] = S.Qf[e];
+  }
+  double* P = reinterpret_cast<double*>(buf + L.P);
+  for (long long e = tid; e < (long long)r * r; e += str) {
+    const int i = (int)(e / r), l = (int)(e - (long long)i * r);
+    P[(size_t)i * S.r_max + l] = S.P[(size_t)i * S.r_max + l];
+  }
+  double* wb = reinterpret_cast<double*>(buf + L.wb);
+  double* u = reinterpret_cast<double*>(buf + L.u);
+  long long* basis = reinterpret_cast<long long*>(buf + L.basis);
+  for (long long e = tid; e < r; e += str) {
+    wb[e] = S.wb[e];
+    u[e] = S.u[e];
+    basis[e] = S.basis_rows[e];
+  }
+  if (tid == 0) {
+    SnapHeader H{};
+    H.magic = SNAP_MAGIC;
+    H.m = S.m;
+    H.ld = S.ld;
+    H.r_max = S.r_max;
+    H.mixed = S.mixed;
+    H.ortho = S.ortho;
+    H.orthog = S.orthog;
+    H.r = r;
+    H.kb = S.ctrl[CTRL_KB];
+    H.pend = S.ctrl[CTRL_PEND];
+    H.rows_seen = *S.rows_seen;
+    *reinterpret_cast<SnapHeader*>(buf) = H;
+    S.ctrl[CTRL_PEND_ROWS] = 0;
+  }
+}
+
+// The inverse copy. A header that does not match the state (other m, r_max or variant, or
+// not a snapshot) sets ST_BADARG and leaves the state unchanged.
+__global__ void restore_kernel(StreamDev S, const unsigned char* buf) {
+  const SnapHeader H = *reinterpret_cast<const SnapHeader*>(buf);
+  const bool ok = H.magic == SNAP_MAGIC && H.m == S.m && H.ld == S.ld && H.r_max == S.r_max &&
+                  H.mixed == S.mixed && H.ortho == S.ortho && H.orthog == S.orthog && H.r >= 0 &&
+                  H.r <= S.r_max;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!ok) {
+    if (tid == 0) atomicOr(S.ctrl + CTRL_STATUS, ST_BADARG);
+    return;
+  }
+  const SnapLayout L = snap_layout(S.ld, S.r_max, S.mixed, S.ortho);
+  const int r = H.r;
+  const long long str = (long long)gridDim.x * blockDim.x;
+  const long long nrow = (long long)r * S.ld;
+  const double* C = reinterpret_cast<const double*>(buf + L.C);
+  const double* Ct = reinterpret_cast<const double*>(buf + L.Ct);
+  const float* Qf = reinterpret_cast<const float*>(buf + L.Qf);
+  for (long long e = tid; e < nrow; e += str) {
+    S.C[e] = C[e];
+    if (!S.ortho) S.Ct[e] = Ct[e];
+    if (S.mixed) S.Qf[e] = Qf[e];
+  }
+  const double* P = reinterpret_cast<const double*>(buf + L.P);
+  for (long long e = tid; e < (long long)r * r; e += str) {
+    const int i = (int)(e / r), l = (int)(e - (long long)i * r);
+    S.P[(size_t)i * S.r_max + l] = P[(size_t)i * S.r_max + l];
+  }
+  const double* wb = reinterpret_cast<const double*>(buf + L.wb);
+  const double* u = reinterpret_cast<const double*>(buf + L.u);
+  const long long* basis = reinterpret_cast<const long long*>(buf + L.basis);
+  for (long long e = tid; e < r; e += str) {
+    S.wb[e] = wb[e];
+    S.u[e] = u[e];
+    S.basis_rows[e] = basis[e];
+  }
+  if (tid == 0) {
+    S.ctrl[CTRL_R] = r;
+    S.ctrl[CTRL_KB] = H.kb;
+    S.ctrl[CTRL_PEND] = H.pend;
+    S.ctrl[CTRL_PEND_ROWS] = 0;
+    S.ctrl[CTRL_STATUS] = 0;
+    *S.rows_seen = H.rows_seen;
+  }
+}
+
+cudaError_t launch_snapshot(const StreamDev& S, void* buf, cudaStream_t stream) {
+  snapshot_kernel<<<64, NT, 0, stream>>>(S, (unsigned char*)buf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restore(const StreamDev& S, const void* buf, cudaStream_t stream) {
+  restore_kernel<<<64, NT, 0, stream>>>(S, (const unsigned char*)buf);
+  return cudaGetLastError();
+}
+
 // Host-side launch helpers (declared in rg_host.h).
 // FP32 projections always come with the orthonormal variant.
-static const void* stream_kernel_ptr(int mixed, int ortho) {
-  if (mixed) return (const void*)stream_kernel<true, true>;
-  return ortho ? (const void*)stream_kernel<false, true> : (const void*)stream_kernel<false, false>;
+static const void* stream_kernel_ptr(int mixed, int ortho, int orthog) {
+  if (mixed) return (const void*)stream_kernel<true, VAR_ORTHONORMAL>;
+  if (ortho) return (const void*)stream_kernel<false, VAR_ORTHONORMAL>;
+  if (orthog) return (const void*)stream_kernel<false, VAR_ORTHOGONAL>;
+  return (const void*)stream_kernel<false, VAR_GENERAL>;
 }
 
 cudaError_t launch_stream(const StreamDev& S, const double* Gamma, const double* y, long long k,
@@ -117,17 +270,17 @@ cudaError_t launch_stream(const StreamDev& S, const double* Gamma, const double*
   CallArgs A{Gamma, y, k, indep};
   StreamDev Sc = S;
   void* args[] = {(void*)&Sc, (void*)&A};
-  return cudaLaunchCooperativeKernel(stream_kernel_ptr(S.mixed, S.ortho), dim3(grid), dim3(NT),
+  return cudaLaunchCooperativeKernel(stream_kernel_ptr(S.mixed, S.ortho, S.orthog), dim3(grid), dim3(NT),
                                      args, 0, stream);
 }
 
-cudaError_t stream_grid_size(int mixed, int ortho, int* grid) {
+cudaError_t stream_grid_size(int mixed, int ortho, int orthog, int* grid) {
   int dev = 0, nsm = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stream_kernel_ptr(mixed, ortho), NT, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stream_kernel_ptr(mixed, ortho, orthog), NT, 0);
   if (e != cudaSuccess) return e;
   *grid = std::min(nsm, 1024) * (per >= 1 ? 1 : 0);  // the section scan holds <= 1024 workers
   return cudaSuccess;

@@ -17,6 +17,7 @@ RG_OK, RG_EINVAL, RG_ENOMEM, RG_ECUDA, RG_ECAPACITY, RG_ENONFINITE, RG_ETIMEOUT 
 RG_FP64, RG_MIXED = 0, 1
 RG_TEST_REL, RG_TEST_PAPER = 0, 2
 RG_ORTHONORMAL = 4  # the orthonormal variant (Section 2.2); implied by RG_MIXED
+RG_ORTHOGONAL = 8  # the orthogonal variant (Section 2.2, alpha = 1); FP64 only
 
 STATUS_NAMES = {0: "RG_OK", 1: "RG_EINVAL", 2: "RG_ENOMEM", 3: "RG_ECUDA", 4: "RG_ECAPACITY",
                 5: "RG_ENONFINITE", 6: "RG_ETIMEOUT"}
@@ -73,6 +74,9 @@ def lib(build: bool = True):
         "rg_set_screen": [vp, f64],
         "rg_batch_set_screen": [vp, f64],
         "rg_batch_set_block_rows": [vp, i64, vp],
+        "rg_snapshot_size": [vp, vp],
+        "rg_snapshot": [vp, vp, i64],
+        "rg_restore": [vp, vp, i64],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -222,6 +226,26 @@ class RankGreville:
         _check(lib().rg_export(self._h, _ptr(C), _ptr(Ct), _ptr(Pinv), _ptr(w), _ptr(basis_rows),
                                int(cap), ctypes.byref(r)), "rg_export")
         return int(r.value)
+
+    def snapshot_size(self) -> int:
+        """rg_snapshot_size: bytes of one snapshot of this state."""
+        out = ctypes.c_int64(0)
+        _check(lib().rg_snapshot_size(self._h, ctypes.byref(out)), "rg_snapshot_size")
+        return int(out.value)
+
+    def new_snapshot_buffer(self, device=None):
+        """A device buffer (uint8 CUDA tensor) that holds one snapshot."""
+        import torch
+        return torch.empty(self.snapshot_size(), dtype=torch.uint8,
+                           device=device if device is not None else torch.cuda.current_device())
+
+    def snapshot(self, buf):
+        """rg_snapshot into buf (uint8 CUDA tensor of at least snapshot_size() bytes)."""
+        _check(lib().rg_snapshot(self._h, _ptr(buf), int(buf.numel())), "rg_snapshot")
+
+    def restore(self, buf):
+        """rg_restore from a snapshot buffer."""
+        _check(lib().rg_restore(self._h, _ptr(buf), int(buf.numel())), "rg_restore")
 
     def close(self):
         if self._h:

@@ -56,3 +56,14 @@ def test_noalloc_binding_rejects_bad_arguments_before_any_launch():
         with pytest.raises(rg.RGError) as ei:
             rg.solve_noalloc(g_, y_, x_)
         assert ei.value.code == rg.RG_EINVAL
+
+
+def test_flag_validation_without_gpu():
+    """rg_init checks its flags before touching the device: the orthogonal variant is
+    FP64-only and excludes the orthonormal one."""
+    import ctypes as ct
+    L = rg.lib()
+    h = ct.c_void_p()
+    for flags in (rg.RG_ORTHOGONAL | rg.RG_MIXED, rg.RG_ORTHOGONAL | rg.RG_ORTHONORMAL, 64):
+        assert L.rg_init(ct.byref(h), 16, 1e-10, flags, 0, None) == rg.RG_EINVAL
+        assert not h.value
