@@ -38,8 +38,19 @@ def _deps():
         os.path.join(CSRC, "*.h")) + [os.path.join(ROOT, "include", "rg.h"), __file__]
 
 
+STAMP = os.path.join(BUILD, "sources.txt")
+
+
+def _source_list() -> str:
+    return "\n".join(os.path.basename(p) for p in sources())
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    """The library exists, is newer than every source and header, and was linked from the
+    sources present now (a removed or added translation unit forces a rebuild)."""
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
+        return False
+    if open(STAMP).read() != _source_list():
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
@@ -73,6 +84,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(_source_list())
     return LIB
 
 

@@ -437,10 +437,17 @@ __device__ void phase_gamma_f32_staged(const Team& T, const StreamDev& S, const 
 }
 
 // A-priori errors D_j = y_j - gamma_j^T w_b of rows [0, b) (Theorems 4/5 with the
-// solution in base coordinates). Warp items, one row each.
+// solution in base coordinates). Warp items, one row each. In the variants of Section 2.2
+// every append extends w_b with 0, so w_b = 0 and D_j = y_j (no FP64 products).
 template <class Team>
 __device__ void phase_dall(const Team& T, const StreamDev& S, const CallArgs& A, long long j0, int b,
                            int r, int w_first = 0) {
+  if (S.ortho || S.orthog) {
+    const long long tstride = (long long)T.size() * NT;
+    const int wid = (T.id() - w_first + T.size()) % T.size();
+    for (long long j = (long long)wid * NT + threadIdx.x; j < b; j += tstride) S.Dall[j] = __ldg(A.y + j0 + j);
+    return;
+  }
   // rows are dealt to the workers starting at w_first (the ones another phase leaves idle)
   const int lane = threadIdx.x & 31;
   const long long wstride = (long long)T.size() * NWARP;
@@ -560,33 +567,6 @@ __device__ void decide_rows_team(const Team& T, const StreamDev& S, const CallAr
 // =======================================================================================
 // Dependent rows: P += gamma gamma^T, u += gamma D for rows of a run whose D are in S.Dall.
 // =======================================================================================
-
-// Compensated FP32 accumulation for mixed mode's Gram sums: blocked summation (FABsum;
-// Blanchard, Higham and Mary, "A class of fast and accurate summation algorithms", SIAM J.
-// Sci. Comput. 42, 2020). The products of FAB_B consecutive rows are summed in FP32 by
-// plain FMAs, and each block sum is added to a pair (s, c) by Knuth's TwoSum, so the error
-// bound is about FAB_B units of FP32 rounding whatever the length of the run (plain FP32
-// accumulation grows with it), for ~1.75 FP32 operations per product. The _rn intrinsics
-// keep the compiler from fusing or reordering the TwoSum steps. The pair is added to the
-// FP64 state as s + c.
-constexpr int FAB_B = 8;
-struct CompSum {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float t = __fadd_rn(s, x);
-    const float z = __fsub_rn(t, s);
-    c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z)));
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return f2d_exact(s) + f2d_exact(c); }
-};
-
-// An FP64 a-priori error D as two FP32 words (D ~ hi + lo to ~48 bits; hi truncated, the
-// remainder D - hi is exact in FP64), so that gamma D enters the FP32 sums as two products.
-__device__ __forceinline__ void split_d(double d, float& hi, float& lo) {
-  hi = d2f_rz(d);
-  lo = d2f_rz(d - f2d_exact(hi));
-}
 
 // Short runs: one thread per entry of P (and of u), dealt round robin over the workers,
 // up to EMAX entries per thread per pass; the gamma rows of the run (and their D) are
@@ -1322,18 +1302,19 @@ __device__ void section_apply_basis(const Team& T, const StreamDev& S, const Cal
 // =======================================================================================
 // Steps 4 and 5 of a block whose rows [0, b) (call rows j0 + [0, b)) have their gamma in
 // S.G, their norms in S.s / S.t and their a-priori errors in S.Dall, and whose first row
-// that needs the sequential section is q0 (b if none): the dependent run before q0, the
+// that needs the sequential section is q0 (b if none): the dependent run before q0 (unless
+// run_done: the tensor-core projection already added it to P and u), the
 // FP64 section from q0 (rank tests in order, appends, fix-ups of the later rows), and the
 // block's bookkeeping (flags, counters, rank, next block size), followed by a team barrier.
 // Returns the rows applied, or -1 if a bounded team barrier gave up.
 template <class Team, bool F32, int VAR>
 __device__ int block_tail(const Team& T, const StreamDev& S, const CallArgs& A, long long j0, int b,
-                          int r, int q0, int kb0) {
+                          int r, int q0, int kb0, bool run_done = false) {
   constexpr bool ORTHO = VAR == VAR_ORTHONORMAL;  // the projection basis is C itself
   __shared__ int shc[3];
   const double* gam = A.Gamma + (size_t)j0 * S.m;
-  // 4: dependent run before the first special row
-  if (q0 > 0 && !dep_run<Team, F32>(T, S, 0, q0, r)) return -1;
+  // 4: dependent run before the first special row (unless already summed: run_done)
+  if (q0 > 0 && !run_done && !dep_run<Team, F32>(T, S, 0, q0, r)) return -1;
   int applied = b, rnew = r;
   if (q0 < b) {
     // 5: sequential section, in FP64 (rows [q0, bend)); its rows never overlap the run
@@ -1401,12 +1382,18 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
     // mixed mode, one CTA per stream, large blocks: projection, rejection norms and the
     // FP32 screen on the tensor cores (q0 = first row the screen cannot clear)
     int q0 = -2;
+    bool gram_done = false;  // the dependent-run sums were fused into the projection
     if constexpr (F32 && std::is_same<Team, CtaTeam>::value) {
       if (S.tcx && b > SMALL_B && r >= 1 && r <= TC_RMAX) {
         double tcut = S.tau_lo;
         if (S.test_mode == 0 && S.tol > 0.0) tcut = fmax(tcut, 0.5 * S.tol);
-        q0 = tc_project_block(reinterpret_cast<TcCtx*>(S.tcx), S, gam, A.y + j0, b, r, tcut);
+        __shared__ bool gd;
+        float* gsm = (r <= TC_GRAM_RMAX && S.Pp && S.pp_cap >= (size_t)r * r && S.up)
+                         ? reinterpret_cast<float*>(smem_pool()) : nullptr;
+        q0 = tc_project_block(reinterpret_cast<TcCtx*>(S.tcx), S, gam, A.y + j0, b, r, tcut, A.k - j0,
+                              gsm, &gd);
         if (q0 < 0) return false;
+        gram_done = gd;
         phase_dall(T, S, A, j0, b, r);
         if (!T.sync()) return false;
       }
@@ -1462,7 +1449,7 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
         q0 = sh[3];
       }
     }
-    const int applied = block_tail<Team, F32, VAR>(T, S, A, j0, b, r, q0, kb0);
+    const int applied = block_tail<Team, F32, VAR>(T, S, A, j0, b, r, q0, kb0, gram_done);
     if (applied < 0) return false;
     j0 += applied;
   }

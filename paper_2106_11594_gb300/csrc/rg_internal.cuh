@@ -44,11 +44,7 @@ enum : int {
   CTRL_PEND_ROWS = 11, // rows of the previous call whose P/u update was deferred (in Gpend)
   CTRL_SUB_COUNT = 32, // barrier counter of the sequential section's column owners (words
                        // 32-33, a cache line apart from the grid barrier's counter)
-  CTRL_SBAR_COUNT = 64,  // the same two counters for the cluster kernel of small calls, whose
-  CTRL_SSUB_COUNT = 96,  // grid has another size (each counter is a multiple of its grid's
-                         // size between launches); words 64-65 and 96-97, own cache lines
-  CTRL_SKEY = 80,      // small calls: 64-bit (call number, first special row) key (words 80-81)
-  CTRL_N = 128
+  CTRL_N = 64
 };
 
 // Everything a kernel needs to know about one stream. Plain pointers into device
@@ -65,7 +61,8 @@ struct StreamDev {
   int orthog;     // 1: orthogonal variant (C and Ct both kept, as in the general variant)
   int test_mode;  // 0 REL, 2 PAPER
   int bar_off = CTRL_BAR_COUNT;  // control words of the grid barrier and of the section's
-  int sub_off = CTRL_SUB_COUNT;  // barrier used by this launch (see CTRL_SBAR_COUNT)
+  int sub_off = CTRL_SUB_COUNT;  // barrier used by this launch (each counter stays a multiple
+                                 // of its team size between launches)
   double tol;     // <= 0: paper default (m^2 r + m r + m) eps_M
   double tau_lo;  // mixed mode: FP32 relative-rejection floor below which rows are dependent
   double* C;      // r_max x ld
@@ -134,6 +131,33 @@ __device__ __forceinline__ double f2d_exact(float f) {
   if (ex == 0u) return man ? (double)f : __hiloint2double((int)sign, 0);
   const unsigned hex = (ex == 0xFFu) ? 0x7FF00000u : ((ex + 896u) << 20);
   return __hiloint2double((int)(sign | hex | (man >> 3)), (int)(man << 29));
+}
+
+// Compensated FP32 accumulation for mixed mode's Gram sums: blocked summation (FABsum;
+// Blanchard, Higham and Mary, "A class of fast and accurate summation algorithms", SIAM J.
+// Sci. Comput. 42, 2020). The products of FAB_B consecutive rows are summed in FP32 by
+// plain FMAs, and each block sum is added to a pair (s, c) by Knuth's TwoSum, so the error
+// bound is about FAB_B units of FP32 rounding whatever the length of the run (plain FP32
+// accumulation grows with it), for ~1.75 FP32 operations per product. The _rn intrinsics
+// keep the compiler from fusing or reordering the TwoSum steps. The pair is added to the
+// FP64 state as s + c.
+constexpr int FAB_B = 8;
+struct CompSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = __fadd_rn(s, x);
+    const float z = __fsub_rn(t, s);
+    c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z)));
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return f2d_exact(s) + f2d_exact(c); }
+};
+
+// An FP64 a-priori error D as two FP32 words (D ~ hi + lo to ~48 bits; hi truncated, the
+// remainder D - hi is exact in FP64), so that gamma D enters the FP32 sums as two products.
+__device__ __forceinline__ void split_d(double d, float& hi, float& lo) {
+  hi = d2f_rz(d);
+  lo = d2f_rz(d - f2d_exact(hi));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

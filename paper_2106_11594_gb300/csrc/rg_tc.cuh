@@ -256,6 +256,19 @@ __device__ __forceinline__ void tc_stage_qt(const TcCtx& X, const float* __restr
   tc_stage_qt_to(X.Bhi, X.Blo, Qf, ld, m, r, c0, k1, t_lo);
 }
 
+// Asks the TMA unit to pull the bytes [p, p + bytes) of global memory into L2 ahead of their
+// use (cp.async.bulk.prefetch: nothing is written to shared memory and nothing waits on it).
+// The range is shrunk inward to 16-byte boundaries, so no byte outside it is touched; it is
+// issued in pieces of at most 32 KiB.
+__device__ __forceinline__ void l2_prefetch(const void* p, size_t bytes) {
+  uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+  const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+  for (; a + 16 <= e; a += 32768) {
+    const uint32_t n = (uint32_t)((e - a) < 32768 ? (e - a) : 32768);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
+  }
+}
+
 // A wait gave up: wait once more (bounded) for the MMAs in flight, so that the caller can
 // release its shared and tensor memory, record ST_TIMEOUT and report failure.
 __device__ __forceinline__ int tc_timeout(const StreamDev& S, TcCtx* Xp, uint32_t ph) {
@@ -265,13 +278,57 @@ __device__ __forceinline__ int tc_timeout(const StreamDev& S, TcCtx* Xp, uint32_
   return -1;
 }
 
-// Block rows [0, b) against the basis (rank 1 <= r <= TC_RMAX), mixed mode, one CTA:
+// Block rows [0, b) against the basis (rank 1 <= r <= TC_RMAX), mixed mode, one CTA (navail:
+// rows available from gam on, for the L2 prefetch of the rows that come next):
 // writes S.G (FP64 copies of the FP32 gammas), S.s and S.t, and returns the first row
 // that the FP32 screen cannot declare dependent (b if none), or -1 if a bounded wait gave
 // up (ST_TIMEOUT is then set in the status word; MMAs may still be in flight). The rows
 // are Gamma[j * m ...] of `gam`, their targets y[j].
+// Dependent-run sums of one chunk, fused into the projection (gsm != null, r <= TC_GRAM_RMAX):
+// the chunk's FP32 gammas are in gsm (row j at gsm + j (r + 1)), its targets as FP32 hi/lo
+// pairs after them; each thread sums entries of the upper triangle of sum_j gamma_j
+// gamma_j^T and of sum_j gamma_j y_j (in the variants of Section 2.2 the a-priori error is
+// y_j, since w_b = 0) over the chunk's rows with FABsum, and adds them to the block's FP64
+// staging sums in S.Pp (triangle, packed by rows) and S.up (first: the block's first chunk).
+constexpr int TC_GRAM_RMAX = 64;
+__device__ __forceinline__ void tc_chunk_gram(const StreamDev& S, const float* gsm, int nrows, int r, bool first) {
+  const int ldg = r + 1;
+  const float* dh = gsm + TC_M * ldg;
+  const float* dl = dh + TC_M;
+  const int ntri = r * (r + 1) / 2;
+  for (int e = threadIdx.x; e < ntri + r; e += NT) {
+    int i, l;
+    if (e < ntri) {  // (i, l), i <= l, rows of the triangle one after another
+      int rem = e;
+      i = 0;
+      while (rem >= r - i) {
+        rem -= r - i;
+        ++i;
+      }
+      l = i + rem;
+    } else {
+      i = e - ntri;
+      l = -1;
+    }
+    CompSum cs;
+    for (int j1 = 0; j1 < nrows; j1 += FAB_B) {
+      const int j2 = min(nrows, j1 + FAB_B);
+      float x = 0.f;
+      if (l >= 0) {
+        for (int j = j1; j < j2; ++j) x = fmaf(gsm[j * ldg + i], gsm[j * ldg + l], x);
+      } else {
+        for (int j = j1; j < j2; ++j) x = fmaf(gsm[j * ldg + i], dh[j], fmaf(gsm[j * ldg + i], dl[j], x));
+      }
+      cs.add(x);
+    }
+    double* dst = (e < ntri) ? S.Pp + e : S.up + i;
+    *dst = (first ? 0.0 : *dst) + cs.value();
+  }
+}
+
 static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const double* __restrict__ gam,
-                                const double* __restrict__ y, int b, int r, double tc) {
+                                const double* __restrict__ y, int b, int r, double tc, long long navail,
+                                float* gsm, bool* gram_done) {
   __shared__ int q0_s;
   const TcCtx X = *Xp;
   uint32_t ph = X.phase;
@@ -307,9 +364,14 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
       Xp->cr = r;
     }
   }
+  if (threadIdx.x == 0) l2_prefetch(gam, (size_t)min(TC_M, b) * m * 8);
   for (int row0 = 0; row0 < b; row0 += TC_M) {
     const int nrows = min(TC_M, b - row0);
     const double* src = gam + (size_t)row0 * m;
+    // the next chunk's rows (of this block, or the first of the next block) into L2 while
+    // this chunk is projected
+    if (threadIdx.x == 0 && row0 + TC_M < navail)
+      l2_prefetch(src + (size_t)TC_M * m, (size_t)min((long long)TC_M, navail - row0 - TC_M) * m * 8);
     // ---- first product: G = Gamma_c Q^T over K slices of m; the next slice's rows are
     // loaded while the tensor cores work on the current one
     double av[16];
@@ -333,7 +395,8 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
       if (ks + 1 < nks) tc_load_a(av, src, m, nrows, (ks + 1) * TC_K);
       if (!tc_wait(X.bar, ph)) return tc_timeout(S, Xp, ph);
     }
-    // ---- G to global (FP64), threads of warps 0-3 own rows
+    // ---- G to global (FP64), threads of warps 0-3 own rows; with the fused dependent-run
+    // sums also the FP32 gammas and the targets to shared memory
     const int row = quarter * 32 + lane;
     if (half == 0) {
       for (int i0 = 0; i0 < n1; i0 += 32) {
@@ -344,8 +407,23 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
 #pragma unroll
           for (int q = 0; q < 32; ++q)
             if (i0 + q < r) gout[i0 + q] = f2d_exact(g[q]);
+          if (gsm) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+              if (i0 + q < r) gsm[row * (r + 1) + i0 + q] = g[q];
+          }
         }
       }
+      if (gsm && row < nrows) {
+        float h, l;
+        split_d(__ldg(y + row0 + row), h, l);
+        gsm[TC_M * (r + 1) + row] = h;
+        gsm[TC_M * (r + 1) + TC_M + row] = l;
+      }
+    }
+    if (gsm) {
+      __syncthreads();
+      tc_chunk_gram(S, gsm, nrows, r, row0 == 0);
     }
     // ---- second product per 64-column slice: GQ, then R = Gamma - GQ and the norms
     float s_acc = 0.f, t_acc = 0.f;
@@ -464,6 +542,28 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
   }
   if (threadIdx.x == 0) Xp->phase = ph;
   const int q0 = q0_s;
+  __syncthreads();
+  // every row of the block dependent: its fused sums go to P (both triangles) and u
+  if (gsm && q0 == b) {
+    const int ntri = r * (r + 1) / 2;
+    for (int e = threadIdx.x; e < ntri + r; e += NT) {
+      if (e < ntri) {
+        int rem = e, i = 0;
+        while (rem >= r - i) {
+          rem -= r - i;
+          ++i;
+        }
+        const int l = i + rem;
+        const double v = __ldcg(S.Pp + e);
+        S.P[(size_t)i * rm + l] = __ldcg(S.P + (size_t)i * rm + l) + v;
+        if (l != i) S.P[(size_t)l * rm + i] = __ldcg(S.P + (size_t)l * rm + i) + v;
+      } else {
+        const int i = e - ntri;
+        S.u[i] = __ldcg(S.u + i) + __ldcg(S.up + i);
+      }
+    }
+  }
+  if (threadIdx.x == 0) *gram_done = gsm != nullptr && q0 == b;
   __syncthreads();
   return q0;
 }
