@@ -888,10 +888,24 @@ __device__ __forceinline__ bool sub_barrier(int* ctrl, int sub_off, int n, unsig
 template <class Team>
 __device__ __forceinline__ bool scan_exchange(const Team& T, const StreamDev& S, double (&v)[32], int nact,
                                               int parity, unsigned long long& bar_target, double* tot,
-                                              double (*wred)[32]) {
+                                              double (*wred)[32], bool warp_active, int nlive) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  warp_transpose_sum32(v);  // lane l holds the warp's sum of value l
-  wred[warp][lane] = v[0];
+  // a warp without columns holds zeros; with at most 16 live values (the later rows of the
+  // section) a 16-value butterfly does (15 FP64 adds instead of 31)
+  if (!warp_active) {
+    wred[warp][lane] = 0.0;
+  } else if (nlive <= 16) {
+    double h[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) h[k] = v[k];
+    const double t16 = warp_transpose_sum<double, 16>(h);
+    const int q = transpose_sum_index<16>();
+    if ((lane & 1) == 0) wred[warp][q] = t16;
+    if (lane >= 16) wred[warp][lane] = 0.0;  // values 16..31: not live
+  } else {
+    warp_transpose_sum32(v);  // lane l holds the warp's sum of value l
+    wred[warp][lane] = v[0];
+  }
   __syncthreads();
   double a = 0.0;
   if (threadIdx.x < 32) {
@@ -1098,7 +1112,8 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
           for (int k = 0; k < 32; ++k)
             if (jj + k < nrow) v[k] = fma(rj, rload(Rb + (size_t)(jj + k) * ldr + c), v[k]);
         }
-        if (!scan_exchange(T, S, v, nact, jj & 1, bar_target, tot, wred)) return false;
+        const bool wact = (long long)T.id() * NT + (threadIdx.x & ~31) < m;  // the warp owns columns
+        if (!scan_exchange(T, S, v, nact, jj & 1, bar_target, tot, wred, wact, nrow - jj)) return false;
         const int d = decide(jj);
         if (d < 0) {
           applied = q0 + jj;
@@ -1107,6 +1122,9 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
         if (d == 1) {
           const double is = is_s;
           const double scale = kv_scale(is, rsq_s);
+          __shared__ double negk[32];  // -kappa_t of the later rows, formed once
+          if (tid < 32) negk[tid] = -tot[tid] * is;
+          __syncthreads();
           for (long long c = col0; c < m; c += cstride) {
             const double rj = rload(Rb + (size_t)jj * ldr + c);
             S.Kv[(size_t)nind * ld + c] = rj * scale;
@@ -1114,7 +1132,7 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
             for (int k = 1; k < 32; ++k)
               if (jj + k < nrow) {
                 double* rt = Rb + (size_t)(jj + k) * ldr + c;
-                *rt = fma(-tot[k] * is, rj, rload(rt));
+                *rt = fma(negk[k], rj, rload(rt));
               }
           }
           ++rc;
