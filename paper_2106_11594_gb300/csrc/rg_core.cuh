@@ -1102,6 +1102,56 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
       }
       auto rload = [&](const double* p) -> double { return rsm ? *p : __ldcg(p); };
       const long long col0 = (long long)T.id() * NT + tid;
+      if (rsm) {
+        // One CTA holds every column, the rejections in shared memory: warp w owns section
+        // rows w, w + 8, w + 16, w + 24. Per row jj each warp forms the products of its rows
+        // t >= jj with row jj (lanes over the columns, one 4-value butterfly; the owner of jj
+        // gets s_jj), so no sum across warps is needed; after the decision each warp fixes
+        // up its own later rows.
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int jj = 0; jj < nrow; ++jj) {
+          const double* rj = Rb + (size_t)jj * ldr;
+          double v[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) v[i] = 0.0;
+          for (int c = lane; c < m; c += 32) {
+            const double x = rj[c];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int t = warp + NWARP * i;
+              if (t >= jj && t < nrow) v[i] = fma(x, Rb[(size_t)t * ldr + c], v[i]);
+            }
+          }
+          warp_transpose_sum<double, 4>(v);
+          if ((lane & 7) == 0) {  // lanes 8 q .. 8 q + 7 hold the total of row warp + NWARP q
+            const int t = warp + NWARP * transpose_sum_index<4>();
+            if (t >= jj && t < nrow) tot[t - jj] = v[0];
+          }
+          __syncthreads();
+          const int d = decide(jj);
+          if (d < 0) {
+            applied = q0 + jj;
+            break;
+          }
+          if (d == 1) {
+            const double is = is_s;
+            const double scale = kv_scale(is, rsq_s);
+            for (int c = tid; c < m; c += NT) S.Kv[(size_t)nind * ld + c] = rj[c] * scale;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int t = warp + NWARP * i;
+              if (t > jj && t < nrow) {
+                const double nk = -tot[t - jj] * is;
+                double* rt = Rb + (size_t)t * ldr;
+                for (int c = lane; c < m; c += 32) rt[c] = fma(nk, rj[c], rt[c]);
+              }
+            }
+            ++rc;
+            ++nind;
+          }
+          __syncthreads();  // the fixed-up rows before the next row's products
+        }
+      } else
       for (int jj = 0; jj < nrow; ++jj) {
         double v[32];
 #pragma unroll
@@ -1210,6 +1260,30 @@ template <class Team, int VAR>
 __device__ void section_apply_pu(const Team& T, const StreamDev& S, int q0, int napp, int r,
                                  int rnew) {
   const int rm = S.r_max;
+  // per-row data of the section, staged once per CTA: flag, rank the row saw, append index,
+  // 1/alpha of an appended row (one FP64 division per row, not per entry) and D
+  __shared__ int fl_s[SLOW_MAX], rj_s[SLOW_MAX], q_s[SLOW_MAX];
+  __shared__ double ia_s[SLOW_MAX], d_s[SLOW_MAX];
+  __syncthreads();
+  if (threadIdx.x < napp) {
+    fl_s[threadIdx.x] = __ldcg(S.rowflag + q0 + threadIdx.x);
+    d_s[threadIdx.x] = __ldcg(S.Dall + q0 + threadIdx.x);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int rj = r, q = 0;
+    for (int jj = 0; jj < napp; ++jj) {
+      rj_s[jj] = rj;
+      q_s[jj] = q;
+      ia_s[jj] = 1.0;
+      if (fl_s[jj] != 1) {
+        if (VAR == VAR_ORTHONORMAL) ia_s[jj] = 1.0 / __ldcg(S.alpha + q);
+        ++rj;
+        ++q;
+      }
+    }
+  }
+  __syncthreads();
   const long long tstride = (long long)T.size() * NT;
   const long long nP = (long long)rnew * rnew;
   for (long long e = rr_thread(T); e < nP + rnew; e += tstride) {
@@ -1217,32 +1291,29 @@ __device__ void section_apply_pu(const Team& T, const StreamDev& S, int q0, int 
     const int i = isP ? (int)(e / rnew) : (int)(e - nP);
     const int l = isP ? (int)(e - (long long)i * rnew) : 0;
     double acc = 0.0;
-    int rj = r, q = 0;
     for (int jj = 0; jj < napp; ++jj) {
-      const int j = q0 + jj;
-      const int flag = __ldcg(S.rowflag + j);
-      const double* g = S.G + (size_t)j * rm;
-      if (flag == 1) {  // dependent
+      const int rj = rj_s[jj];
+      const double* g = S.G + (size_t)(q0 + jj) * rm;
+      if (fl_s[jj] == 1) {  // dependent
         if (isP) {
           if (i < rj && l < rj) acc = fma(__ldcg(g + i), __ldcg(g + l), acc);
         } else if (i < rj) {
-          acc = fma(__ldcg(g + i), __ldcg(S.Dall + j), acc);
+          acc = fma(__ldcg(g + i), d_s[jj], acc);
         }
       } else {  // independent: opens entry rj
         if (VAR != VAR_GENERAL) {  // g = [gamma_j; 1/alpha_j], alpha = 1 (orthogonal)
-          const double ia = VAR == VAR_ORTHONORMAL ? 1.0 / __ldcg(S.alpha + q) : 1.0;
-          const double gi = (i < rj) ? __ldcg(S.Gind + (size_t)q * rm + i) : (i == rj ? ia : 0.0);
+          const double ia = ia_s[jj];
+          const double* gq = S.Gind + (size_t)q_s[jj] * rm;
+          const double gi = (i < rj) ? __ldcg(gq + i) : (i == rj ? ia : 0.0);
           if (isP) {
-            const double gl = (l < rj) ? __ldcg(S.Gind + (size_t)q * rm + l) : (l == rj ? ia : 0.0);
+            const double gl = (l < rj) ? __ldcg(gq + l) : (l == rj ? ia : 0.0);
             acc = fma(gi, gl, acc);
           } else {
-            acc = fma(gi, __ldcg(S.Dall + j), acc);
+            acc = fma(gi, d_s[jj], acc);
           }
         } else if (isP && i == rj && l == rj) {
           acc += 1.0;
         }
-        ++rj;
-        ++q;
       }
     }
     if (isP) {

@@ -310,15 +310,33 @@ __device__ __forceinline__ void tc_chunk_gram(const StreamDev& S, const float* g
       i = e - ntri;
       l = -1;
     }
+    // FP32 blocks of FAB_B rows in two FMA chains, unrolled so that the block's shared-memory
+    // loads issue together; block sums compensated
     CompSum cs;
-    for (int j1 = 0; j1 < nrows; j1 += FAB_B) {
-      const int j2 = min(nrows, j1 + FAB_B);
-      float x = 0.f;
+    const float* ga = gsm + i;
+    const float* gb = gsm + (l >= 0 ? l : 0);
+    int j1 = 0;
+    for (; j1 + FAB_B <= nrows; j1 += FAB_B) {
+      float x0 = 0.f, x1 = 0.f;
       if (l >= 0) {
-        for (int j = j1; j < j2; ++j) x = fmaf(gsm[j * ldg + i], gsm[j * ldg + l], x);
+#pragma unroll
+        for (int j = j1; j < j1 + FAB_B; j += 2) {
+          x0 = fmaf(ga[j * ldg], gb[j * ldg], x0);
+          x1 = fmaf(ga[(j + 1) * ldg], gb[(j + 1) * ldg], x1);
+        }
       } else {
-        for (int j = j1; j < j2; ++j) x = fmaf(gsm[j * ldg + i], dh[j], fmaf(gsm[j * ldg + i], dl[j], x));
+#pragma unroll
+        for (int j = j1; j < j1 + FAB_B; j += 2) {
+          x0 = fmaf(ga[j * ldg], dh[j], fmaf(ga[j * ldg], dl[j], x0));
+          x1 = fmaf(ga[(j + 1) * ldg], dh[j + 1], fmaf(ga[(j + 1) * ldg], dl[j + 1], x1));
+        }
       }
+      cs.add(x0 + x1);
+    }
+    if (j1 < nrows) {  // the last, partial block
+      float x = 0.f;
+      for (int j = j1; j < nrows; ++j)
+        x = (l >= 0) ? fmaf(ga[j * ldg], gb[j * ldg], x) : fmaf(ga[j * ldg], dh[j], fmaf(ga[j * ldg], dl[j], x));
       cs.add(x);
     }
     double* dst = (e < ntri) ? S.Pp + e : S.up + i;
