@@ -279,6 +279,24 @@ __device__ void phase_gamma_cta(const Team& T, const StreamDev& S, const double*
   }
 }
 
+// FP32 screen of mixed mode: true if the row is certainly dependent (relative rejection
+// at most tc). Rows whose squared norm leaves the range where FP32 squares and sums are
+// exact enough (including zero rows) are not screened: the FP64 section decides them.
+__device__ __forceinline__ bool fp32_screen_dependent(double s, double t, double tc) {
+  return t > 1e-30 && t < 1e30 && s <= tc * tc * t;
+}
+
+// The rank decisions of a small block fused into its rejection phase (grid teams): the CTA
+// whose item completes a row group's partial norms (one counter per group, control words
+// CTRL_GRP..) sums the group's partials in a fixed order, decides its rows as decide_rows
+// does, stores s and t, lowers CTRL_Q0 to the first row that needs the sequential section,
+// and clears the counter for the next block. After the phase's barrier every CTA reads
+// CTRL_Q0 instead of reducing and deciding every row itself.
+struct FusedDecide {
+  const double* y;  // the block's targets
+  double tc;        // mixed mode: floor of the FP32 screen
+};
+
 // Gamma_r = Gamma_j - B^T gamma_j with B = C (general) or Q (orthonormal). CTA item =
 // (4 RPT rows) x (MC columns): thread (row lane rl, column cc) handles rows rl, rl + 4,
 // ..., so each staged basis tile serves 4 RPT rows. The basis tile (RC ranks x MC
@@ -291,7 +309,7 @@ __device__ void phase_gamma_cta(const Team& T, const StreamDev& S, const double*
 template <class Team, bool F32, int RPT>
 __device__ void phase_reject(const Team& T, const StreamDev& S, const double* __restrict__ gam,
                              int row_lo, int row_hi, int r, const double* __restrict__ back64,
-                             double* __restrict__ Rout) {
+                             double* __restrict__ Rout, const FusedDecide* fd = nullptr) {
   using V = typename std::conditional<F32, float, double>::type;
   constexpr int RB = 4 * RPT;                          // rows per item
   constexpr int RC = (F32 || RPT == 1) ? 64 : 32;      // ranks per staged chunk
@@ -394,6 +412,44 @@ __device__ void phase_reject(const Team& T, const StreamDev& S, const double* __
         S.tpart[(size_t)jr * nmc + mc] = red_t[2 * rla][q] + red_t[2 * rla + 1][q];
       }
     }
+    if (fd) {  // the group's last item decides its rows (see FusedDecide)
+      __shared__ int last_s;
+      if (threadIdx.x < RB) __threadfence();  // the partials before the counter
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        last_s = atomicAdd(S.ctrl + CTRL_GRP + grp, 1) == nmc - 1;
+      }
+      __syncthreads();
+      if (last_s) {
+        __threadfence();
+        // one warp per row: lanes load the partials (all in flight together), a butterfly
+        // sums them in a fixed order
+        for (int a = warp; a < RB; a += NWARP) {
+          const int jr = jb + a;
+          if (jr >= row_hi) continue;
+          double sv = 0.0, tv = 0.0;
+          for (int c = lane; c < nmc; c += 32) {
+            sv += __ldcg(S.spart + (size_t)jr * nmc + c);
+            tv += __ldcg(S.tpart + (size_t)jr * nmc + c);
+          }
+          sv = warp_sum(sv);
+          tv = warp_sum(tv);
+          if (lane == 0) {
+            S.s[jr] = sv;
+            S.t[jr] = tv;
+            const double yv = __ldg(fd->y + jr);
+            bool special = !isfinite(tv) || !isfinite(yv);
+            if (!special) {
+              if (F32) special = !fp32_screen_dependent(sv, tv, fd->tc);
+              else special = is_independent(sv, tv, r, S.m, S.tol, S.test_mode);
+            }
+            if (special) atomicMin(S.ctrl + CTRL_Q0, jr);
+          }
+        }
+        if (threadIdx.x == 0) S.ctrl[CTRL_GRP + grp] = 0;
+      }
+    }
   }
 }
 
@@ -462,12 +518,6 @@ __device__ void phase_dall(const Team& T, const StreamDev& S, const CallArgs& A,
   }
 }
 
-// FP32 screen of mixed mode: true if the row is certainly dependent (relative rejection
-// at most tc). Rows whose squared norm leaves the range where FP32 squares and sums are
-// exact enough (including zero rows) are not screened: the FP64 section decides them.
-__device__ __forceinline__ bool fp32_screen_dependent(double s, double t, double tc) {
-  return t > 1e-30 && t < 1e30 && s <= tc * tc * t;
-}
 
 // Reduce the partial norms of rows [0, b), decide every row and return the first row that
 // needs the sequential section (independent, FP32 candidate, or non-finite). Every CTA that
@@ -1500,9 +1550,14 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       else
         phase_gamma<Team, F32>(T, S, gam, 0, b, r, ORTHO ? S.C : S.Ct);
       if (!T.sync()) return false;
-      // 2: rejections and norms; a-priori errors against w_b
-      if (big_rej) phase_reject<Team, F32, 8>(T, S, gam, 0, b, r, S.C, nullptr);
-      else phase_reject<Team, F32, 1>(T, S, gam, 0, b, r, S.C, nullptr);
+      // 2: rejections and norms (grid teams, small blocks: with the decisions fused in);
+      // a-priori errors against w_b
+      constexpr bool kGridTeam = std::is_same<Team, GridTeam>::value;
+      const bool fuse = kGridTeam && b <= SMALL_B && (b + 3) / 4 <= 16;
+      FusedDecide fdv{A.y + j0, S.tau_lo};
+      if (F32 && S.test_mode == 0 && S.tol > 0.0) fdv.tc = fmax(fdv.tc, 0.5 * S.tol);
+      if (big_rej) phase_reject<Team, F32, 8>(T, S, gam, 0, b, r, S.C, nullptr, fuse ? &fdv : nullptr);
+      else phase_reject<Team, F32, 1>(T, S, gam, 0, b, r, S.C, nullptr, fuse ? &fdv : nullptr);
       // CTAs beyond the rejection items take the a-priori errors and the previous call's
       // deferred P/u update
       const long long nrej = (long long)((b + 4 * (big_rej ? 8 : 1) - 1) / (4 * (big_rej ? 8 : 1))) * S.nmc;
@@ -1512,7 +1567,13 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       if (!T.sync()) return false;
       // 3: decide
       if (b <= SMALL_B) {
-        q0 = decide_rows<F32>(S, A, j0, b, r, T.id() == 0);
+        if (fuse) {
+          if (threadIdx.x == 0) sh[3] = __ldcg(S.ctrl + CTRL_Q0);  // decided before the barrier
+          __syncthreads();
+          q0 = sh[3];
+        } else {
+          q0 = decide_rows<F32>(S, A, j0, b, r, T.id() == 0);
+        }
         if (q0 == b) {  // fast finish: every row dependent
           const bool defer = S.defer && last && j0 == 0;  // the call's only block
           if (!defer) acc_small<Team, F32>(T, S, 0, b, r);

@@ -44,6 +44,8 @@ enum : int {
   CTRL_PEND_ROWS = 11, // rows of the previous call whose P/u update was deferred (in Gpend)
   CTRL_SUB_COUNT = 32, // barrier counter of the sequential section's column owners (words
                        // 32-33, a cache line apart from the grid barrier's counter)
+  CTRL_GRP = 40,       // 16 words: per-row-group item counters of the decision fused into
+                       // the rejection phase of small blocks (idle between blocks: zero)
   CTRL_N = 64
 };
 
