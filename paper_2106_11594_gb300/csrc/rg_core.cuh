@@ -279,11 +279,153 @@ __device__ void phase_gamma_cta(const Team& T, const StreamDev& S, const double*
   }
 }
 
+// Small blocks on grid teams: CTA tile = JT rows x BT basis rows (BT in {1, 2, 4, 8}, from
+// small_gamma_bt). Warp w takes basis row w % BT of the tile over the column range w / BT of
+// NWARP / BT equal ranges, so the four SM sub-partitions (warp w on w % 4), each with its
+// own FP64 unit, get equal shares of every tile. The lanes stride over the range with the
+// JT row sums in registers (each basis element loaded serves JT rows); one butterfly
+// transpose-reduction combines them across the lanes and the ranges are added in shared
+// memory in a fixed order. A warp does 4 m BT / 256 FMAs per lane before its 6 adds, where
+// phase_gamma_cta does 32 before 9.
+template <class Team, bool F32, int JT>
+__device__ void phase_gamma_small(const Team& T, const StreamDev& S, const double* __restrict__ gam,
+                                  int row_lo, int row_hi, int r, const double* __restrict__ basis64, int BT) {
+  using V = typename std::conditional<F32, float, double>::type;
+  const int nrows = row_hi - row_lo;
+  if (nrows <= 0 || r <= 0) return;
+  const int m = S.m, ld = S.ld, rm = S.r_max;
+  const int ntb = (r + BT - 1) / BT, ntj = (nrows + JT - 1) / JT;
+  const long long ntiles = (long long)ntj * ntb;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nseg = NWARP / BT, seg = warp / BT, bb = warp - seg * BT;
+  const int len = ((m + nseg - 1) / nseg + 31) & ~31;  // columns per range (multiple of 32)
+  const int c_lo = seg * len, c_hi = min(m, c_lo + len);
+  __shared__ double red[NWARP][JT];
+  for (long long it = T.id(); it < ntiles; it += T.size()) {
+    const int tj = (int)(it / ntb), tb = (int)(it - (long long)tj * ntb);
+    const int j0 = row_lo + tj * JT, i = tb * BT + bb;
+    const bool iok = i < r;
+    const double* gp = gam + (size_t)j0 * m;
+    V acc[JT];
+#pragma unroll
+    for (int a = 0; a < JT; ++a) acc[a] = V(0);
+#pragma unroll 8
+    for (int c = c_lo + lane; c < c_hi; c += 32) {
+      V gv[JT];
+#pragma unroll
+      for (int a = 0; a < JT; ++a) gv[a] = (j0 + a < row_hi) ? (V)__ldg(gp + (size_t)a * m + c) : V(0);
+      V bv;
+      if (F32) bv = iok ? (V)__ldcg(S.Qf + (size_t)i * ld + c) : V(0);
+      else bv = iok ? (V)__ldcg(basis64 + (size_t)i * ld + c) : V(0);
+#pragma unroll
+      for (int a = 0; a < JT; ++a) acc[a] = fma(bv, gv[a], acc[a]);
+    }
+    const V tot = warp_transpose_sum<V, JT>(acc);
+    const int q = transpose_sum_index<JT>();
+    if ((lane & (32 / JT - 1)) == 0) red[warp][q] = (double)tot;
+    __syncthreads();
+    if (threadIdx.x < JT * BT) {
+      const int a = threadIdx.x / BT, b2 = threadIdx.x - a * BT;
+      double v = 0.0;
+      for (int s2 = 0; s2 < nseg; ++s2) v += red[s2 * BT + b2][a];
+      const int ii = tb * BT + b2;
+      if (j0 + a < row_hi && ii < r) S.G[(size_t)(j0 + a) * rm + ii] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Basis rows per tile of phase_gamma_small for ntj row groups, rank r and nw workers. FP64:
+// the fewest FMAs per sub-partition (rounds x BT), ties to the larger BT (fewer adds and
+// rounds); FP32, where the FMAs are cheap: the fewest rounds, ties to the smaller BT (less
+// data per CTA).
+__device__ __forceinline__ int small_gamma_bt(int ntj, int r, int nw, bool f32) {
+  int best = 1;
+  long long bc = -1;
+  for (int bt = 1; bt <= NWARP; bt <<= 1) {
+    const long long tiles = (long long)ntj * ((r + bt - 1) / bt);
+    const long long rounds = (tiles + nw - 1) / nw;
+    const long long cost = f32 ? rounds * 16 + bt : rounds * bt * 16 - bt;
+    if (bc < 0 || cost < bc) {
+      bc = cost;
+      best = bt;
+    }
+  }
+  return best;
+}
+
+template <class Team, bool F32>
+__device__ __forceinline__ void phase_gamma_small_any(const Team& T, const StreamDev& S, const double* gam,
+                                                      int row_lo, int row_hi, int r, const double* basis64) {
+  const int nrows = row_hi - row_lo;
+  const int jt = nrows >= 4 ? 4 : (nrows >= 2 ? 2 : 1);
+  const int bt = small_gamma_bt((nrows + jt - 1) / jt, r, T.size(), F32);
+  if (jt == 4) phase_gamma_small<Team, F32, 4>(T, S, gam, row_lo, row_hi, r, basis64, bt);
+  else if (jt == 2) phase_gamma_small<Team, F32, 2>(T, S, gam, row_lo, row_hi, r, basis64, bt);
+  else phase_gamma_small<Team, F32, 1>(T, S, gam, row_lo, row_hi, r, basis64, bt);
+}
+
 // FP32 screen of mixed mode: true if the row is certainly dependent (relative rejection
 // at most tc). Rows whose squared norm leaves the range where FP32 squares and sums are
 // exact enough (including zero rows) are not screened: the FP64 section decides them.
 __device__ __forceinline__ bool fp32_screen_dependent(double s, double t, double tc) {
   return t > 1e-30 && t < 1e30 && s <= tc * tc * t;
+}
+
+// TMA prefetch of the basis tile of a CTA's first rejection item (grid teams, small blocks):
+// rows [0, rc) x columns [mc MC, mc MC + MC) of C (FP64) or of the FP32 copy of Q (mixed
+// mode), one bulk copy per basis row into the shared-memory pool, issued before the
+// projection so that the copies overlap it and the barrier after it. A copy stops at the
+// row stride ld (a multiple of 4 elements, so every copy is a multiple of 16 bytes and
+// starts on a 16-byte boundary of the 256-byte aligned state); the columns >= m it brings
+// are never used. phase_reject then waits for the tile (bounded) instead of staging it.
+struct RejPrefetch {
+  unsigned long long* bar;  // mbarrier: one arrival with the expected bytes per prefetch
+  uint32_t* ph;             // parity of its next completion (per thread)
+};
+
+// One bulk copy (TMA) of `bytes` from global to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Every thread waits for the completion of parity ph of the mbarrier (bounded); the CTA
+// agrees on the outcome. On success the parity advances; false if the wait gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t& ph) {
+  bool done = mbar_try_wait(bar, ph);
+  if (!done) {
+    const unsigned long long t0 = global_ns();
+    while (!(done = mbar_try_wait(bar, ph)))
+      if (global_ns() - t0 > WAIT_LIMIT_NS) break;
+  }
+  if (!__syncthreads_and(done ? 1 : 0)) return false;
+  ph ^= 1u;
+  return true;
+}
+
+template <bool F32>
+__device__ __forceinline__ void rej_prefetch(const StreamDev& S, int mc, int rc, unsigned long long* bar) {
+  fence_async_smem();  // earlier generic accesses of the pool before the asynchronous writes
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    constexpr int ES = F32 ? 4 : 8;
+    const uint32_t bytes = (uint32_t)(min(MC, S.ld - mc * MC) * ES);
+    if (threadIdx.x == 0)
+      asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                       smem_u32(bar)),
+                   "r"(bytes * (uint32_t)rc)
+                   : "memory");
+    __syncwarp();
+    const char* src = F32 ? reinterpret_cast<const char*>(S.Qf) : reinterpret_cast<const char*>(S.C);
+    src += (size_t)mc * MC * ES;
+    char* dst = reinterpret_cast<char*>(smem_pool());
+    for (int ii = threadIdx.x; ii < rc; ii += 32)
+      bulk_g2s(dst + (size_t)ii * MC * ES, src + (size_t)ii * S.ld * ES, bytes, bar);
+  }
 }
 
 // The rank decisions of a small block fused into its rejection phase (grid teams): the CTA
@@ -309,7 +451,8 @@ struct FusedDecide {
 template <class Team, bool F32, int RPT>
 __device__ void phase_reject(const Team& T, const StreamDev& S, const double* __restrict__ gam,
                              int row_lo, int row_hi, int r, const double* __restrict__ back64,
-                             double* __restrict__ Rout, const FusedDecide* fd = nullptr) {
+                             double* __restrict__ Rout, const FusedDecide* fd = nullptr,
+                             const RejPrefetch* pf = nullptr) {
   using V = typename std::conditional<F32, float, double>::type;
   constexpr int RB = 4 * RPT;                          // rows per item
   constexpr int RC = (F32 || RPT == 1) ? 64 : 32;      // ranks per staged chunk
@@ -341,18 +484,28 @@ __device__ void phase_reject(const Team& T, const StreamDev& S, const double* __
     }
     for (int i0 = 0; i0 < r; i0 += RC) {
       const int rc = min(RC, r - i0);
+      const bool prefetched = pf && i0 == 0 && it == T.id();  // see RejPrefetch
       __syncthreads();
+      if (!prefetched) {
 #pragma unroll 8
-      for (int e = threadIdx.x; e < rc * MC; e += NT) {
-        const int ii = e / MC, c2 = mc * MC + (e - ii * MC);
-        if (F32) Bt[e] = (c2 < m) ? (V)__ldcg(S.Qf + (size_t)(i0 + ii) * ld + c2) : V(0);
-        else Bt[e] = (c2 < m) ? (V)__ldcg(back64 + (size_t)(i0 + ii) * ld + c2) : V(0);
+        for (int e = threadIdx.x; e < rc * MC; e += NT) {
+          const int ii = e / MC, c2 = mc * MC + (e - ii * MC);
+          if (F32) Bt[e] = (c2 < m) ? (V)__ldcg(S.Qf + (size_t)(i0 + ii) * ld + c2) : V(0);
+          else Bt[e] = (c2 < m) ? (V)__ldcg(back64 + (size_t)(i0 + ii) * ld + c2) : V(0);
+        }
       }
 #pragma unroll 4
       for (int e = threadIdx.x; e < RB * rc; e += NT) {
         const int a = e / rc, ii = e - a * rc;
         const int ja = jb + a;
         Gs[a * RC + ii] = (ja < row_hi) ? (V)__ldcg(S.G + (size_t)ja * rm + i0 + ii) : V(0);
+      }
+      if (prefetched && !mbar_wait(pf->bar, *pf->ph)) {
+        // the tile never arrived: flag the failure, wait once more (bounded) for the copies
+        // in flight, and go on with whatever the pool holds (the status word stops the call)
+        if (threadIdx.x == 0) atomicOr(S.ctrl + CTRL_STATUS, ST_TIMEOUT);
+        uint32_t p2 = *pf->ph;
+        if (mbar_wait(pf->bar, p2)) *pf->ph = p2;
       }
       __syncthreads();
       int ii = 0;
@@ -1458,7 +1611,9 @@ __device__ int block_tail(const Team& T, const StreamDev& S, const CallArgs& A, 
   if (q0 < b) {
     // 5: sequential section, in FP64 (rows [q0, bend)); its rows never overlap the run
     const int bend = min(b, q0 + SLOW_MAX);
-    if ((long long)((bend - q0 + 7) / 8) * r < 4LL * NWARP * T.size())
+    if (std::is_same<Team, GridTeam>::value)
+      phase_gamma_small_any<Team, false>(T, S, gam, q0, bend, r, ORTHO ? S.C : S.Ct);
+    else if ((long long)((bend - q0 + 7) / 8) * r < 4LL * NWARP * T.size())
       phase_gamma_cta(T, S, gam, q0, bend, r, ORTHO ? S.C : S.Ct);
     else
       phase_gamma<Team, false>(T, S, gam, q0, bend, r, ORTHO ? S.C : S.Ct);
@@ -1502,6 +1657,21 @@ template <class Team, bool F32, int VAR = (F32 ? VAR_ORTHONORMAL : VAR_GENERAL)>
 __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& A) {
   constexpr bool ORTHO = VAR == VAR_ORTHONORMAL;  // the projection basis is C itself
   __shared__ int sh[8];
+  constexpr bool kGridTeam = std::is_same<Team, GridTeam>::value;
+  __shared__ __align__(8) unsigned long long pf_bar;  // rejection-tile prefetch (RejPrefetch)
+  uint32_t pf_ph = 0;
+  if (kGridTeam && threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&pf_bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // grid teams: the call's first rows (up to a small block) into L2 while the control
+  // words are read, each CTA asking for its share
+  if (kGridTeam && threadIdx.x == 0) {
+    const size_t bytes = (size_t)min(A.k, (long long)SMALL_B) * S.m * 8;
+    const size_t share = ((bytes + T.size() - 1) / T.size() + 255) & ~(size_t)255;
+    const size_t off = share * T.id();
+    if (off < bytes) l2_prefetch(reinterpret_cast<const char*>(A.Gamma) + off, min(share, bytes - off));
+  }
   long long j0 = 0;
   while (j0 < A.k) {
     if (threadIdx.x == 0) {  // written before the last barrier or by an earlier launch
@@ -1543,21 +1713,32 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       // larger items only while they still give every worker at least two
       const bool big_rej = (long long)(b / 32) * S.nmc >= 2LL * T.size();
       const int gr = min(8, (int)((POOL_DOUBLES * 2) / max(S.m, 1)));  // FP32 rows that fit
-      if (F32 && gr >= 1 && (long long)(b / gr) >= 2LL * T.size())
+      // grid teams, small blocks: the basis tile of this CTA's first rejection item comes
+      // in by TMA while the projection runs
+      const bool pf_on = kGridTeam && b <= SMALL_B && !big_rej && r > 0 &&
+                         (long long)T.id() < (long long)((b + 3) / 4) * S.nmc;
+      if (pf_on) rej_prefetch<F32>(S, (int)(T.id() % S.nmc), min(64, r), &pf_bar);
+      RejPrefetch pfv{&pf_bar, &pf_ph};
+      if (kGridTeam && b <= SMALL_B)
+        phase_gamma_small_any<Team, F32>(T, S, gam, 0, b, r, ORTHO ? S.C : S.Ct);
+      else if (F32 && gr >= 1 && (long long)(b / gr) >= 2LL * T.size())
         phase_gamma_f32_staged(T, S, gam, 0, b, r, gr);
       else if (!F32 && (long long)((b + 7) / 8) * r < 4LL * NWARP * T.size())
         phase_gamma_cta(T, S, gam, 0, b, r, ORTHO ? S.C : S.Ct);  // few warp items: split each over a CTA
       else
         phase_gamma<Team, F32>(T, S, gam, 0, b, r, ORTHO ? S.C : S.Ct);
-      if (!T.sync()) return false;
+      if (!T.sync()) {
+        if (pf_on) mbar_wait(&pf_bar, pf_ph);  // no copy may be in flight at exit
+        return false;
+      }
       // 2: rejections and norms (grid teams, small blocks: with the decisions fused in);
       // a-priori errors against w_b
-      constexpr bool kGridTeam = std::is_same<Team, GridTeam>::value;
       const bool fuse = kGridTeam && b <= SMALL_B && (b + 3) / 4 <= 16;
       FusedDecide fdv{A.y + j0, S.tau_lo};
       if (F32 && S.test_mode == 0 && S.tol > 0.0) fdv.tc = fmax(fdv.tc, 0.5 * S.tol);
       if (big_rej) phase_reject<Team, F32, 8>(T, S, gam, 0, b, r, S.C, nullptr, fuse ? &fdv : nullptr);
-      else phase_reject<Team, F32, 1>(T, S, gam, 0, b, r, S.C, nullptr, fuse ? &fdv : nullptr);
+      else phase_reject<Team, F32, 1>(T, S, gam, 0, b, r, S.C, nullptr, fuse ? &fdv : nullptr,
+                                      pf_on ? &pfv : nullptr);
       // CTAs beyond the rejection items take the a-priori errors and the previous call's
       // deferred P/u update
       const long long nrej = (long long)((b + 4 * (big_rej ? 8 : 1) - 1) / (4 * (big_rej ? 8 : 1))) * S.nmc;
