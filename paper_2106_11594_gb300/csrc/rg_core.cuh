@@ -1688,19 +1688,18 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
     const bool last = (j0 + b == A.k);
     const double* gam = A.Gamma + (size_t)j0 * S.m;
     __syncthreads();
-    // mixed mode, one CTA per stream, large blocks: projection, rejection norms and the
-    // FP32 screen on the tensor cores (q0 = first row the screen cannot clear)
+    // mixed mode, one CTA per stream: projection, rejection norms and the FP32 screen on
+    // the tensor cores (q0 = first row the screen cannot clear)
     int q0 = -2;
     bool gram_done = false;  // the dependent-run sums were fused into the projection
     if constexpr (F32 && std::is_same<Team, CtaTeam>::value) {
-      if (S.tcx && b > SMALL_B && r >= 1 && r <= TC_RMAX) {
+      if (S.tcx && r >= 1 && r <= TC_RMAX) {
         double tcut = S.tau_lo;
         if (S.test_mode == 0 && S.tol > 0.0) tcut = fmax(tcut, 0.5 * S.tol);
         __shared__ bool gd;
-        float* gsm = (r <= TC_GRAM_RMAX && S.Pp && S.pp_cap >= (size_t)r * r && S.up)
-                         ? reinterpret_cast<float*>(smem_pool()) : nullptr;
+        const bool want_gram = S.Pp && S.pp_cap >= (size_t)r * r && S.up;
         q0 = tc_project_block(reinterpret_cast<TcCtx*>(S.tcx), S, gam, A.y + j0, b, r, tcut, A.k - j0,
-                              gsm, &gd);
+                              reinterpret_cast<float*>(smem_pool()), want_gram, &gd);
         if (q0 < 0) return false;
         gram_done = gd;
         phase_dall(T, S, A, j0, b, r);

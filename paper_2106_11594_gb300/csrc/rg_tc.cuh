@@ -284,13 +284,14 @@ __device__ __forceinline__ int tc_timeout(const StreamDev& S, TcCtx* Xp, uint32_
 // that the FP32 screen cannot declare dependent (b if none), or -1 if a bounded wait gave
 // up (ST_TIMEOUT is then set in the status word; MMAs may still be in flight). The rows
 // are Gamma[j * m ...] of `gam`, their targets y[j].
-// Dependent-run sums of one chunk, fused into the projection (gsm != null, r <= TC_GRAM_RMAX):
-// the chunk's FP32 gammas are in gsm (row j at gsm + j (r + 1)), its targets as FP32 hi/lo
+// Dependent-run sums of one chunk, fused into the projection (gsm != null): the chunk's
+// FP32 gammas are in gsm (row j at gsm + j (r + 1)), its targets as FP32 hi/lo
 // pairs after them; each thread sums entries of the upper triangle of sum_j gamma_j
 // gamma_j^T and of sum_j gamma_j y_j (in the variants of Section 2.2 the a-priori error is
 // y_j, since w_b = 0) over the chunk's rows with FABsum, and adds them to the block's FP64
 // staging sums in S.Pp (triangle, packed by rows) and S.up (first: the block's first chunk).
-constexpr int TC_GRAM_RMAX = 64;
+constexpr int TC_GRAM_RMAX = 64;  // staging in the shared pool up to this rank (above it: see
+                                  // tc_project_block)
 __device__ __forceinline__ void tc_chunk_gram(const StreamDev& S, const float* gsm, int nrows, int r, bool first) {
   const int ldg = r + 1;
   const float* dh = gsm + TC_M * ldg;
@@ -346,7 +347,7 @@ __device__ __forceinline__ void tc_chunk_gram(const StreamDev& S, const float* g
 
 static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const double* __restrict__ gam,
                                 const double* __restrict__ y, int b, int r, double tc, long long navail,
-                                float* gsm, bool* gram_done) {
+                                float* pool, bool want_gram, bool* gram_done) {
   __shared__ int q0_s;
   const TcCtx X = *Xp;
   uint32_t ph = X.phase;
@@ -381,6 +382,15 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
       Xp->cq = S.Qf;
       Xp->cr = r;
     }
+  }
+  // staging of the fused dependent-run sums (tc_chunk_gram): the chunk's FP32 gammas and
+  // targets go to the shared pool up to rank TC_GRAM_RMAX; above it, to the dynamic shared
+  // memory after the per-slice B tiles, which is free whenever the B-tile cache is not in use
+  // (always the case above rank 64, where the cache no longer fits)
+  float* gsm = nullptr;
+  if (want_gram) {
+    if (r <= TC_GRAM_RMAX) gsm = pool;
+    else if (!cached && TC_M * (r + 1) + 2 * TC_M <= X.cache_cap - 2 * TC_TILE) gsm = X.Bhi + 2 * TC_TILE;
   }
   if (threadIdx.x == 0) l2_prefetch(gam, (size_t)min(TC_M, b) * m * 8);
   for (int row0 = 0; row0 < b; row0 += TC_M) {
