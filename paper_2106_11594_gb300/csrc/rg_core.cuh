@@ -439,6 +439,51 @@ struct FusedDecide {
   double tc;        // mixed mode: floor of the FP32 screen
 };
 
+// The fused decision (FusedDecide) of row group grp, rows [jb, min(jb + rb, row_hi)), called by
+// every thread of an item once its partial norms are written (by threads [0, rb)).
+template <bool F32>
+__device__ __forceinline__ void fused_decide(const StreamDev& S, const FusedDecide* fd, int grp, int jb, int rb,
+                                             int row_hi, int r) {
+  const int nmc = S.nmc;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ int last_s;
+  if (threadIdx.x < rb) __threadfence();  // the partials before the counter
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last_s = atomicAdd(S.ctrl + CTRL_GRP + grp, 1) == nmc - 1;
+  }
+  __syncthreads();
+  if (last_s) {
+    __threadfence();
+    // one warp per row: lanes load the partials (all in flight together), a butterfly sums
+    // them in a fixed order
+    for (int a = warp; a < rb; a += NWARP) {
+      const int jr = jb + a;
+      if (jr >= row_hi) continue;
+      double sv = 0.0, tv = 0.0;
+      for (int c = lane; c < nmc; c += 32) {
+        sv += __ldcg(S.spart + (size_t)jr * nmc + c);
+        tv += __ldcg(S.tpart + (size_t)jr * nmc + c);
+      }
+      sv = warp_sum(sv);
+      tv = warp_sum(tv);
+      if (lane == 0) {
+        S.s[jr] = sv;
+        S.t[jr] = tv;
+        const double yv = __ldg(fd->y + jr);
+        bool special = !isfinite(tv) || !isfinite(yv);
+        if (!special) {
+          if (F32) special = !fp32_screen_dependent(sv, tv, fd->tc);
+          else special = is_independent(sv, tv, r, S.m, S.tol, S.test_mode);
+        }
+        if (special) atomicMin(S.ctrl + CTRL_Q0, jr);
+      }
+    }
+    if (threadIdx.x == 0) S.ctrl[CTRL_GRP + grp] = 0;
+  }
+}
+
 // Gamma_r = Gamma_j - B^T gamma_j with B = C (general) or Q (orthonormal). CTA item =
 // (4 RPT rows) x (MC columns): thread (row lane rl, column cc) handles rows rl, rl + 4,
 // ..., so each staged basis tile serves 4 RPT rows. The basis tile (RC ranks x MC
@@ -565,44 +610,91 @@ __device__ void phase_reject(const Team& T, const StreamDev& S, const double* __
         S.tpart[(size_t)jr * nmc + mc] = red_t[2 * rla][q] + red_t[2 * rla + 1][q];
       }
     }
-    if (fd) {  // the group's last item decides its rows (see FusedDecide)
-      __shared__ int last_s;
-      if (threadIdx.x < RB) __threadfence();  // the partials before the counter
+    if (fd) fused_decide<F32>(S, fd, grp, jb, RB, row_hi, r);
+  }
+}
+
+// Blocks of at most 16 rows on grid teams: CTA item = 1 row x MC columns (the 4-row items
+// of phase_reject would carry empty rows). Thread (warp w, lane) takes column 8 w +
+// (lane mod 8) of the item and every fourth rank from lane / 8 on, so it does a quarter of
+// the FMAs of a 4-row item's thread; two shuffles combine the quarters. The partial norms
+// per (row, column chunk), the basis-tile prefetch and the fused decision are those of
+// phase_reject.
+template <class Team, bool F32>
+__device__ void phase_reject_row(const Team& T, const StreamDev& S, const double* __restrict__ gam,
+                                 int row_lo, int row_hi, int r, const double* __restrict__ back64,
+                                 const FusedDecide* fd, const RejPrefetch* pf) {
+  using V = typename std::conditional<F32, float, double>::type;
+  constexpr int RC = 64;  // ranks per staged chunk, as phase_reject with 4-row items
+  static_assert(RC * MC * sizeof(V) / 8 + RC * sizeof(V) / 8 <= POOL_DOUBLES, "pool");
+  const int nrows = row_hi - row_lo;
+  if (nrows <= 0) return;
+  const int m = S.m, ld = S.ld, nmc = S.nmc, rm = S.r_max;
+  const long long nitems = (long long)nrows * nmc;
+  __shared__ double red_s[NWARP], red_t[NWARP];
+  V* Bt = reinterpret_cast<V*>(smem_pool());  // RC x MC basis tile
+  V* Gs = Bt + RC * MC;                        // RC gammas of the row
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cc = warp * 8 + (lane & 7), qr = lane >> 3;
+  for (long long it = T.id(); it < nitems; it += T.size()) {
+    const int grp = (int)(it / nmc);
+    const int mc = (int)(it - (long long)grp * nmc);
+    const int j = row_lo + grp;
+    const int c = mc * MC + cc;
+    const double gv = (c < m) ? __ldg(gam + (size_t)j * m + c) : 0.0;
+    V acc = (qr == 0) ? (V)gv : V(0);
+    for (int i0 = 0; i0 < r; i0 += RC) {
+      const int rc = min(RC, r - i0);
+      const bool prefetched = pf && i0 == 0 && it == T.id();  // see RejPrefetch
       __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        last_s = atomicAdd(S.ctrl + CTRL_GRP + grp, 1) == nmc - 1;
-      }
-      __syncthreads();
-      if (last_s) {
-        __threadfence();
-        // one warp per row: lanes load the partials (all in flight together), a butterfly
-        // sums them in a fixed order
-        for (int a = warp; a < RB; a += NWARP) {
-          const int jr = jb + a;
-          if (jr >= row_hi) continue;
-          double sv = 0.0, tv = 0.0;
-          for (int c = lane; c < nmc; c += 32) {
-            sv += __ldcg(S.spart + (size_t)jr * nmc + c);
-            tv += __ldcg(S.tpart + (size_t)jr * nmc + c);
-          }
-          sv = warp_sum(sv);
-          tv = warp_sum(tv);
-          if (lane == 0) {
-            S.s[jr] = sv;
-            S.t[jr] = tv;
-            const double yv = __ldg(fd->y + jr);
-            bool special = !isfinite(tv) || !isfinite(yv);
-            if (!special) {
-              if (F32) special = !fp32_screen_dependent(sv, tv, fd->tc);
-              else special = is_independent(sv, tv, r, S.m, S.tol, S.test_mode);
-            }
-            if (special) atomicMin(S.ctrl + CTRL_Q0, jr);
-          }
+      if (!prefetched) {
+#pragma unroll 8
+        for (int e = threadIdx.x; e < rc * MC; e += NT) {
+          const int ii = e / MC, c2 = mc * MC + (e - ii * MC);
+          if (F32) Bt[e] = (c2 < m) ? (V)__ldcg(S.Qf + (size_t)(i0 + ii) * ld + c2) : V(0);
+          else Bt[e] = (c2 < m) ? (V)__ldcg(back64 + (size_t)(i0 + ii) * ld + c2) : V(0);
         }
-        if (threadIdx.x == 0) S.ctrl[CTRL_GRP + grp] = 0;
       }
+      for (int e = threadIdx.x; e < rc; e += NT) Gs[e] = (V)__ldcg(S.G + (size_t)j * rm + i0 + e);
+      if (prefetched && !mbar_wait(pf->bar, *pf->ph)) {
+        if (threadIdx.x == 0) atomicOr(S.ctrl + CTRL_STATUS, ST_TIMEOUT);
+        uint32_t p2 = *pf->ph;
+        if (mbar_wait(pf->bar, p2)) *pf->ph = p2;
+      }
+      __syncthreads();
+      // ranks qr, qr + 4, ...: the four lane groups read four different banks of Gs
+      V a0 = V(0), a1 = V(0);
+      int ii = qr;
+      for (; ii + 4 < rc; ii += 8) {
+        a0 = fma(-Bt[ii * MC + cc], Gs[ii], a0);
+        a1 = fma(-Bt[(ii + 4) * MC + cc], Gs[ii + 4], a1);
+      }
+      if (ii < rc) a0 = fma(-Bt[ii * MC + cc], Gs[ii], a0);
+      acc += a0 + a1;
     }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    const bool own = qr == 0 && c < m;  // lanes 0-7 hold the warp's 8 columns
+    V two[2] = {own ? acc * acc : V(0), own ? (V)gv * (V)gv : V(0)};
+    const V tot = warp_transpose_sum<V, 2>(two);
+    const int qi = transpose_sum_index<2>();
+    if ((lane & 15) == 0) {
+      if (qi == 0) red_s[warp] = (double)tot;
+      else red_t[warp] = (double)tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sv = 0.0, tv = 0.0;
+#pragma unroll
+      for (int w = 0; w < NWARP; ++w) {
+        sv += red_s[w];
+        tv += red_t[w];
+      }
+      S.spart[(size_t)j * nmc + mc] = sv;
+      S.tpart[(size_t)j * nmc + mc] = tv;
+    }
+    if (fd) fused_decide<F32>(S, fd, grp, j, 1, row_hi, r);
+    else __syncthreads();  // red_s / red_t are free for the next item
   }
 }
 
@@ -1714,8 +1806,18 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       const int gr = min(8, (int)((POOL_DOUBLES * 2) / max(S.m, 1)));  // FP32 rows that fit
       // grid teams, small blocks: the basis tile of this CTA's first rejection item comes
       // in by TMA while the projection runs
-      const bool pf_on = kGridTeam && b <= SMALL_B && !big_rej && r > 0 &&
-                         (long long)T.id() < (long long)((b + 3) / 4) * S.nmc;
+      // FP64: one-row rejection items (phase_reject_row) when they take fewer FMA
+      // instructions per SM sub-partition over the grid's rounds: 48 per round (16 FMAs and
+      // the combining adds per thread) against 128 for the 4-row items (FP32 FMAs are cheap:
+      // mixed mode keeps the 4-row items)
+      bool row_rej = false;
+      if (!F32 && kGridTeam && b <= 16 && r > 0) {
+        const long long r1 = ((long long)b * S.nmc + T.size() - 1) / T.size();
+        const long long r4 = ((long long)((b + 3) / 4) * S.nmc + T.size() - 1) / T.size();
+        row_rej = r1 * 48 < r4 * 128;
+      }
+      const long long rej_items = row_rej ? (long long)b * S.nmc : (long long)((b + 3) / 4) * S.nmc;
+      const bool pf_on = kGridTeam && b <= SMALL_B && !big_rej && r > 0 && (long long)T.id() < rej_items;
       if (pf_on) rej_prefetch<F32>(S, (int)(T.id() % S.nmc), min(64, r), &pf_bar);
       RejPrefetch pfv{&pf_bar, &pf_ph};
       if (kGridTeam && b <= SMALL_B)
@@ -1736,11 +1838,14 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
       FusedDecide fdv{A.y + j0, S.tau_lo};
       if (F32 && S.test_mode == 0 && S.tol > 0.0) fdv.tc = fmax(fdv.tc, 0.5 * S.tol);
       if (big_rej) phase_reject<Team, F32, 8>(T, S, gam, 0, b, r, S.C, nullptr, fuse ? &fdv : nullptr);
+      else if (!F32 && row_rej) phase_reject_row<Team, false>(T, S, gam, 0, b, r, S.C, fuse ? &fdv : nullptr,
+                                                              pf_on ? &pfv : nullptr);
       else phase_reject<Team, F32, 1>(T, S, gam, 0, b, r, S.C, nullptr, fuse ? &fdv : nullptr,
                                       pf_on ? &pfv : nullptr);
       // CTAs beyond the rejection items take the a-priori errors and the previous call's
       // deferred P/u update
-      const long long nrej = (long long)((b + 4 * (big_rej ? 8 : 1) - 1) / (4 * (big_rej ? 8 : 1))) * S.nmc;
+      const long long nrej = row_rej ? (long long)b * S.nmc
+                                     : (long long)((b + 4 * (big_rej ? 8 : 1) - 1) / (4 * (big_rej ? 8 : 1))) * S.nmc;
       const int w_lo = (int)min(nrej, (long long)max(0, T.size() - 16));
       phase_dall(T, S, A, j0, b, r, w_lo);
       if (sh[4] > 0) acc_rows<Team, F32>(T, S, S.Gpend, S.Dpend, 0, sh[4], r, w_lo);
