@@ -143,32 +143,7 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, co
   extern __shared__ __align__(1024) unsigned char dyn_smem[];
   float* const dyn_base = reinterpret_cast<float*>(
       (reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~static_cast<uintptr_t>(1023));
-  if (MIXED) {
-    if (threadIdx.x < 32) {  // warp 0 owns the allocation
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tc_tmem)),
-                   "r"(TC_TMEM_COLS));
-      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (threadIdx.x == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tc_bar)));
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-      float* base = dyn_base;
-      tcx.Ahi = base;
-      tcx.Alo = base + TC_TILE;
-      tcx.Bhi = base + 2 * TC_TILE;
-      tcx.Blo = base + 3 * TC_TILE;
-      tcx.bar = &tc_bar;
-      tcx.phase = 0;
-      tcx.cache_cap = (TC_SMEM_MIXED - 1024) / 4 - 2 * TC_TILE;
-      tcx.cq = nullptr;
-      tcx.cr = -1;
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (threadIdx.x == 0) tcx.tmem = tc_tmem;
-    __syncthreads();
-  }
+  if (MIXED) tc_ctx_init(&tcx, &tc_bar, &tc_tmem, dyn_base, TC_SMEM_MIXED);
   StreamDev S{};
   S.tcx = MIXED ? (void*)&tcx : nullptr;
   S.Rs = reinterpret_cast<double*>(dyn_base);
@@ -216,13 +191,7 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, co
     }
     if (!ok) break;  // a bounded wait gave up: stop taking work
   }
-  if (MIXED) {
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (threadIdx.x < 32)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tcx.tmem), "r"(TC_TMEM_COLS));
-  }
+  if (MIXED) tc_ctx_release(&tcx);
 }
 
 // FP32 projections always come with the orthonormal variant.

@@ -1108,6 +1108,34 @@ __device__ void gram_reduce(const Team& T, const StreamDev& S, int r, int nch) {
   }
 }
 
+// The grid team's tensor-core chunk path: P (both triangles) and u += the per-CTA staging
+// slots [0, nslot) of the fused dependent-run sums (slot c: packed triangle at
+// S.Pp + c r (r + 1) / 2, sums of gamma_j y_j at S.up + c r), added in slot order.
+template <class Team>
+__device__ void gram_reduce_slots(const Team& T, const StreamDev& S, int r, int nslot) {
+  const int rm = S.r_max;
+  const long long ntri = (long long)r * (r + 1) / 2;
+  const long long tstride = (long long)T.size() * NT;
+  for (long long e = rr_thread(T); e < ntri + r; e += tstride) {
+    double acc = 0.0;
+    if (e < ntri) {
+      for (int c = 0; c < nslot; ++c) acc += __ldcg(S.Pp + (size_t)c * ntri + e);
+      int rem = (int)e, i = 0;
+      while (rem >= r - i) {
+        rem -= r - i;
+        ++i;
+      }
+      const int l = i + rem;
+      S.P[(size_t)i * rm + l] = __ldcg(S.P + (size_t)i * rm + l) + acc;
+      if (l != i) S.P[(size_t)l * rm + i] = __ldcg(S.P + (size_t)l * rm + i) + acc;
+    } else {
+      const int i = (int)(e - ntri);
+      for (int c = 0; c < nslot; ++c) acc += __ldcg(S.up + (size_t)c * r + i);
+      S.u[i] = __ldcg(S.u + i) + acc;
+    }
+  }
+}
+
 template <class Team, bool F32>
 __device__ __forceinline__ void acc_small(const Team& T, const StreamDev& S, int a, int len, int r) {
   acc_rows<Team, F32>(T, S, S.G, S.Dall, a, len, r, 0);
@@ -1745,7 +1773,9 @@ __device__ int block_tail(const Team& T, const StreamDev& S, const CallArgs& A, 
   return applied;
 }
 
-template <class Team, bool F32, int VAR = (F32 ? VAR_ORTHONORMAL : VAR_GENERAL)>
+// TCG: the kernel carries the tensor-core chunk path of large mixed-mode blocks on a grid
+// team (stream_tc_kernel); the other grid kernels leave it out.
+template <class Team, bool F32, int VAR = (F32 ? VAR_ORTHONORMAL : VAR_GENERAL), bool TCG = false>
 __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& A) {
   constexpr bool ORTHO = VAR == VAR_ORTHONORMAL;  // the projection basis is C itself
   __shared__ int sh[8];
@@ -1791,9 +1821,61 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
         __shared__ bool gd;
         const bool want_gram = S.Pp && S.pp_cap >= (size_t)r * r && S.up;
         q0 = tc_project_block(reinterpret_cast<TcCtx*>(S.tcx), S, gam, A.y + j0, b, r, tcut, A.k - j0,
-                              reinterpret_cast<float*>(smem_pool()), want_gram, &gd);
+                              reinterpret_cast<float*>(smem_pool()), want_gram, &gd,
+                              TcOut{0, S.Pp, S.up, true, true});
         if (q0 < 0) return false;
         gram_done = gd;
+        phase_dall(T, S, A, j0, b, r);
+        if (!T.sync()) return false;
+      }
+    }
+    // mixed mode, whole GPU, blocks of at least TC_GRID_MIN rows: the same tensor-core
+    // projection, each CTA taking 128-row chunks of the block (q0 = the first row that any
+    // chunk's screen cannot clear; the CTAs' fused sums are reduced when there is none)
+    if constexpr (F32 && kGridTeam && TCG) {
+      if (S.tcx && b >= TC_GRID_MIN && r >= 1 && r <= TC_RMAX) {
+        double tcut = S.tau_lo;
+        if (S.test_mode == 0 && S.tol > 0.0) tcut = fmax(tcut, 0.5 * S.tol);
+        const int nchunk = (b + TC_M - 1) / TC_M;
+        const int nslot = min(T.size(), nchunk);
+        const size_t ntri = (size_t)r * (r + 1) / 2;
+        const bool want_gram = S.Pp && S.up && (size_t)nslot * ntri <= S.pp_cap &&
+                               (size_t)nslot * r <= (size_t)NCH_MAX * S.r_max;
+        __shared__ bool gd;
+        int q_loc = b;
+        bool sums_ok = want_gram, first = true;
+        for (int ch = T.id(); ch < nchunk; ch += T.size()) {
+          const int c0 = ch * TC_M, nr = min(TC_M, b - c0);
+          const int q = tc_project_block(reinterpret_cast<TcCtx*>(S.tcx), S, gam + (size_t)c0 * S.m,
+                                         A.y + j0 + c0, nr, r, tcut, A.k - j0 - c0,
+                                         reinterpret_cast<float*>(smem_pool()), want_gram, &gd,
+                                         TcOut{c0, want_gram ? S.Pp + (size_t)T.id() * ntri : nullptr,
+                                               want_gram ? S.up + (size_t)T.id() * r : nullptr, first, false});
+          if (q < 0) return false;
+          if (q < nr) q_loc = min(q_loc, c0 + q);
+          sums_ok = sums_ok && gd;
+          first = false;
+        }
+        if (threadIdx.x == 0 && T.id() < nslot) {  // this CTA's first special row, sums usable
+          S.spart[2 * T.id()] = (double)q_loc;
+          S.spart[2 * T.id() + 1] = sums_ok ? 1.0 : 0.0;
+        }
+        if (!T.sync()) return false;
+        __shared__ int q_all;
+        if (threadIdx.x == 0) q_all = b;
+        __syncthreads();
+        bool ok_mine = true;
+        for (int c = threadIdx.x; c < nslot; c += NT) {
+          const int qc = (int)__ldcg(S.spart + 2 * c);
+          if (qc < b) atomicMin(&q_all, qc);
+          ok_mine = ok_mine && __ldcg(S.spart + 2 * c + 1) != 0.0;
+        }
+        const bool ok_all = __syncthreads_and(ok_mine ? 1 : 0) != 0;
+        q0 = q_all;
+        if (want_gram && ok_all && q0 == b) {
+          gram_reduce_slots(T, S, r, nslot);
+          gram_done = true;
+        }
         phase_dall(T, S, A, j0, b, r);
         if (!T.sync()) return false;
       }

@@ -235,8 +235,9 @@ rg_status rg_init(rg_state** out, int64_t m, double tol, int flags, int64_t r_ma
   S.tol = tol;
   S.tau_lo = 1e-5;
   S.nmc = (int)((m + MC - 1) / MC);
-  // internal block: large enough to fill the GPU, bounded so the scratch stays small
-  long long kb = 4096;
+  // internal block: large enough to fill the GPU (mixed mode: to give every SM tensor-core
+  // chunks), bounded so the scratch stays small
+  long long kb = S.mixed ? 32768 : 4096;
   while (kb > 256 && (double)kb * (double)r_max * 8.0 > 256.0 * (1 << 20)) kb /= 2;
   S.kb_max = (int)kb;
   {  // Gram-path partials: at least one chunk at full rank, up to NCH_MAX, <= 128 MiB

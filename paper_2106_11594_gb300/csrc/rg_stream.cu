@@ -49,6 +49,26 @@ __global__ void __launch_bounds__(NT, 1) stream_kernel(StreamDev S, CallArgs A) 
   process_rows<GridTeam, F32, VAR>(GridTeam{S.ctrl}, S, A);
 }
 
+// Mixed mode, calls of at least TC_GRID_MIN rows: a separate instantiation, launched with
+// TC_SMEM bytes of dynamic shared memory for the tensor-core chunk path (the small-call
+// kernel keeps its whole L1); each CTA holds its tensor-memory columns for the call.
+__global__ void __launch_bounds__(NT, 1) stream_tc_kernel(StreamDev S, CallArgs A) {
+  __shared__ TcCtx tcx;
+  __shared__ __align__(8) unsigned long long tc_bar;
+  __shared__ uint32_t tc_tmem;
+  extern __shared__ __align__(1024) unsigned char dyn_smem[];
+  grid_barrier_init(S.ctrl);
+  const bool tc_on = dyn_smem_bytes() >= (uint32_t)TC_SMEM;
+  if (tc_on) {
+    float* const dyn_base = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~static_cast<uintptr_t>(1023));
+    tc_ctx_init(&tcx, &tc_bar, &tc_tmem, dyn_base, TC_SMEM);
+    S.tcx = &tcx;
+  }
+  process_rows<GridTeam, true, VAR_ORTHONORMAL, true>(GridTeam{S.ctrl}, S, A);
+  if (tc_on) tc_ctx_release(&tcx);
+}
+
 // Folds the P/u update deferred by the last small call (if any) into P and u: every CTA
 // takes entries; the next kernel on the stream (form_w_kernel, export_prep_kernel) clears
 // the pending count.
@@ -270,6 +290,9 @@ cudaError_t launch_stream(const StreamDev& S, const double* Gamma, const double*
   CallArgs A{Gamma, y, k, indep};
   StreamDev Sc = S;
   void* args[] = {(void*)&Sc, (void*)&A};
+  if (S.mixed && k >= TC_GRID_MIN)
+    return cudaLaunchCooperativeKernel((const void*)stream_tc_kernel, dim3(grid), dim3(NT), args, TC_SMEM,
+                                       stream);
   return cudaLaunchCooperativeKernel(stream_kernel_ptr(S.mixed, S.ortho, S.orthog), dim3(grid), dim3(NT),
                                      args, 0, stream);
 }
@@ -282,6 +305,14 @@ cudaError_t stream_grid_size(int mixed, int ortho, int orthog, int* grid) {
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stream_kernel_ptr(mixed, ortho, orthog), NT, 0);
   if (e != cudaSuccess) return e;
+  if (mixed) {  // the kernel of large calls, with the tensor-core chunk path's operand tiles
+    int per_tc = 0;
+    e = cudaFuncSetAttribute((const void*)stream_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_tc, (const void*)stream_tc_kernel, NT, TC_SMEM);
+    if (e != cudaSuccess) return e;
+    per = std::min(per, per_tc);
+  }
   *grid = std::min(nsm, 1024) * (per >= 1 ? 1 : 0);  // the section scan holds <= 1024 workers
   return cudaSuccess;
 }

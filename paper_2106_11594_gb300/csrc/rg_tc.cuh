@@ -59,6 +59,10 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// Blocks of at least this many rows of a single mixed-mode stream take the tensor-core
+// chunk path on the whole GPU (every SM gets a 128-row chunk from 152 x 128 / 2 rows on).
+constexpr int TC_GRID_MIN = 8192;
+
 // Offset (floats) of element (row, k) in a tile with a 32-wide K slice.
 __host__ __device__ __forceinline__ int tc_off(int row, int k) {
   return (row >> 3) * 256 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
@@ -256,6 +260,51 @@ __device__ __forceinline__ void tc_stage_qt(const TcCtx& X, const float* __restr
   tc_stage_qt_to(X.Bhi, X.Blo, Qf, ld, m, r, c0, k1, t_lo);
 }
 
+__device__ __forceinline__ uint32_t dyn_smem_bytes() {
+  uint32_t x;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(x));
+  return x;
+}
+
+// The CTA's tensor-core context over `smem_bytes` of dynamic shared memory at dyn_base
+// (1024-byte aligned): warp 0 allocates TC_TMEM_COLS columns of tensor memory (one CTA per
+// SM, so they are always free), thread 0 initialises the mbarrier and lays out the operand
+// tiles Ahi, Alo, Bhi, Blo, the rest after Bhi being the B-tile cache. Every thread calls
+// it; tc_ctx_release frees the tensor memory before the CTA exits.
+__device__ __forceinline__ void tc_ctx_init(TcCtx* tcx, unsigned long long* bar, uint32_t* tmem_slot,
+                                            float* dyn_base, int smem_bytes) {
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    tcx->Ahi = dyn_base;
+    tcx->Alo = dyn_base + TC_TILE;
+    tcx->Bhi = dyn_base + 2 * TC_TILE;
+    tcx->Blo = dyn_base + 3 * TC_TILE;
+    tcx->bar = bar;
+    tcx->phase = 0;
+    tcx->cache_cap = (smem_bytes - 1024) / 4 - 2 * TC_TILE;
+    tcx->cq = nullptr;
+    tcx->cr = -1;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x == 0) tcx->tmem = *tmem_slot;
+  __syncthreads();
+}
+__device__ __forceinline__ void tc_ctx_release(const TcCtx* tcx) {
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tcx->tmem), "r"(TC_TMEM_COLS));
+}
+
 // Asks the TMA unit to pull the bytes [p, p + bytes) of global memory into L2 ahead of their
 // use (cp.async.bulk.prefetch: nothing is written to shared memory and nothing waits on it).
 // The range is shrunk inward to 16-byte boundaries, so no byte outside it is touched; it is
@@ -288,11 +337,12 @@ __device__ __forceinline__ int tc_timeout(const StreamDev& S, TcCtx* Xp, uint32_
 // FP32 gammas are in gsm (row j at gsm + j (r + 1)), its targets as FP32 hi/lo
 // pairs after them; each thread sums entries of the upper triangle of sum_j gamma_j
 // gamma_j^T and of sum_j gamma_j y_j (in the variants of Section 2.2 the a-priori error is
-// y_j, since w_b = 0) over the chunk's rows with FABsum, and adds them to the block's FP64
-// staging sums in S.Pp (triangle, packed by rows) and S.up (first: the block's first chunk).
+// y_j, since w_b = 0) over the chunk's rows with FABsum, and adds them to FP64 staging sums:
+// pp (the triangle, packed by rows) and upp (first: the staging's first chunk).
 constexpr int TC_GRAM_RMAX = 64;  // staging in the shared pool up to this rank (above it: see
                                   // tc_project_block)
-__device__ __forceinline__ void tc_chunk_gram(const StreamDev& S, const float* gsm, int nrows, int r, bool first) {
+__device__ __forceinline__ void tc_chunk_gram(double* __restrict__ pp, double* __restrict__ upp, const float* gsm,
+                                              int nrows, int r, bool first) {
   const int ldg = r + 1;
   const float* dh = gsm + TC_M * ldg;
   const float* dl = dh + TC_M;
@@ -340,14 +390,27 @@ __device__ __forceinline__ void tc_chunk_gram(const StreamDev& S, const float* g
         x = (l >= 0) ? fmaf(ga[j * ldg], gb[j * ldg], x) : fmaf(ga[j * ldg], dh[j], fmaf(ga[j * ldg], dl[j], x));
       cs.add(x);
     }
-    double* dst = (e < ntri) ? S.Pp + e : S.up + i;
+    double* dst = (e < ntri) ? pp + e : upp + i;
     *dst = (first ? 0.0 : *dst) + cs.value();
   }
 }
 
+// Where tc_project_block's rows land and where its fused dependent-run sums go. A one-CTA
+// team projects a whole block (jb = 0) and commits the sums to P and u itself when every
+// row is dependent; a CTA of a grid team projects chunks of a block (jb = the chunk's
+// first row), sums into its own staging slot across its chunks (first: its first chunk)
+// and leaves the reduction over the slots to the team.
+struct TcOut {
+  int jb;        // block row of the first row: G, s and t are written at jb + j
+  double* pp;    // staging triangle (null: no fused sums)
+  double* upp;   // staging sums of gamma_j y_j
+  bool first;    // the staging starts with this call
+  bool commit;   // add the staging to P and u when every row is dependent
+};
+
 static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const double* __restrict__ gam,
                                 const double* __restrict__ y, int b, int r, double tc, long long navail,
-                                float* pool, bool want_gram, bool* gram_done) {
+                                float* pool, bool want_gram, bool* gram_done, const TcOut& O) {
   __shared__ int q0_s;
   const TcCtx X = *Xp;
   uint32_t ph = X.phase;
@@ -388,7 +451,7 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
   // memory after the per-slice B tiles, which is free whenever the B-tile cache is not in use
   // (always the case above rank 64, where the cache no longer fits)
   float* gsm = nullptr;
-  if (want_gram) {
+  if (want_gram && O.pp) {
     if (r <= TC_GRAM_RMAX) gsm = pool;
     else if (!cached && TC_M * (r + 1) + 2 * TC_M <= X.cache_cap - 2 * TC_TILE) gsm = X.Bhi + 2 * TC_TILE;
   }
@@ -431,7 +494,7 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
         float g[32];
         tmem_ld32(d1 + lane_base + (uint32_t)i0, g);
         if (row < nrows) {
-          double* gout = S.G + (size_t)(row0 + row) * rm;
+          double* gout = S.G + (size_t)(O.jb + row0 + row) * rm;
 #pragma unroll
           for (int q = 0; q < 32; ++q)
             if (i0 + q < r) gout[i0 + q] = f2d_exact(g[q]);
@@ -451,7 +514,7 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
     }
     if (gsm) {
       __syncthreads();
-      tc_chunk_gram(S, gsm, nrows, r, row0 == 0);
+      tc_chunk_gram(O.pp, O.upp, gsm, nrows, r, O.first && row0 == 0);
     }
     // ---- second product per 64-column slice: GQ, then R = Gamma - GQ and the norms
     float s_acc = 0.f, t_acc = 0.f;
@@ -561,8 +624,8 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
     if (half == 0 && row < nrows) {
       const double s = (double)(s_acc + red_s[row]), t = (double)(t_acc + red_t[row]);
       const int j = row0 + row;
-      S.s[j] = s;
-      S.t[j] = t;
+      S.s[O.jb + j] = s;
+      S.t[O.jb + j] = t;
       const double yv = __ldg(y + j);
       if (!isfinite(yv) || !(t > 1e-30 && t < 1e30 && s <= tc * tc * t)) atomicMin(&q0_s, j);
     }
@@ -572,7 +635,7 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
   const int q0 = q0_s;
   __syncthreads();
   // every row of the block dependent: its fused sums go to P (both triangles) and u
-  if (gsm && q0 == b) {
+  if (gsm && O.commit && q0 == b) {
     const int ntri = r * (r + 1) / 2;
     for (int e = threadIdx.x; e < ntri + r; e += NT) {
       if (e < ntri) {
@@ -582,12 +645,12 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
           ++i;
         }
         const int l = i + rem;
-        const double v = __ldcg(S.Pp + e);
+        const double v = __ldcg(O.pp + e);
         S.P[(size_t)i * rm + l] = __ldcg(S.P + (size_t)i * rm + l) + v;
         if (l != i) S.P[(size_t)l * rm + i] = __ldcg(S.P + (size_t)l * rm + i) + v;
       } else {
         const int i = e - ntri;
-        S.u[i] = __ldcg(S.u + i) + __ldcg(S.up + i);
+        S.u[i] = __ldcg(S.u + i) + __ldcg(O.upp + i);
       }
     }
   }
