@@ -91,6 +91,47 @@ def test_full_size_large_stream_mixed_one_call():
     assert checks.rel_err(g["X"], o.X) <= TOLMIX
 
 
+def _late_growth_stream(n, m, rank, late, seed):
+    """Rows in a rank-`rank` row space (the first `rank` rows grow it), except the rows in
+    `late`, which each bring one new direction; Y = A x + noise 1e-3."""
+    rng = np.random.default_rng(seed)
+    extra = len(late)
+    G2 = rng.standard_normal((rank + extra, m))
+    F = np.zeros((n, rank + extra))
+    F[:, :rank] = rng.standard_normal((n, rank))
+    for q, j in enumerate(late):
+        F[j, rank + q] = 1.0 + rng.random()
+    A = np.ascontiguousarray(F @ G2)
+    Y = A @ rng.standard_normal(m) + 1e-3 * rng.standard_normal(n)
+    return A, Y
+
+
+@pytest.mark.parametrize("case", ["ragged", "late_growth", "rank_80"])
+def test_mixed_large_calls_tensor_core_blocks(case):
+    """One mixed-mode call of >= 8192 rows runs its blocks of >= 8192 rows through the
+    tensor-core chunk path on the whole GPU. The blocks double from 64 rows after the last
+    rank change, so with m = 512:
+      ragged      - rank 40; blocks of 8192 rows at row 8192 and of 8200 rows at 16384
+                    (65 chunks, the last of 8 rows);
+      late_growth - as ragged, plus two new directions at rows 20000 and 20001, inside the
+                    8200-row block: the chunks' fused sums are discarded, the 3616 rows before
+                    the first are summed again from G, and the FP64 section takes both;
+      rank_80     - rank 80 (above the shared-memory staging of the fused sums): the
+                    8192-row block at row 8224 sums its rows from G.
+    Flags and basis rows as integer arrays and X within 1e-4 of the FP64 oracle."""
+    n, m = {"ragged": (24584, 512), "late_growth": (24584, 512), "rank_80": (16416, 512)}[case]
+    rank = 80 if case == "rank_80" else 40
+    late = [20000, 20001] if case == "late_growth" else []
+    A, Y = _late_growth_stream(n, m, rank, late, seed={"ragged": 11, "late_growth": 12, "rank_80": 13}[case])
+    o = fp64.solve(A, Y, tol=1e-10)
+    assert o.rank == rank + len(late)
+    g = run_stream(A, Y, n, mode=rg.RG_MIXED, export=True)
+    assert g["rank"] == o.rank
+    np.testing.assert_array_equal(g["indep"], o.indep)
+    np.testing.assert_array_equal(g["basis"], o.basis_rows)
+    assert checks.rel_err(g["X"], o.X) <= TOLMIX, checks.rel_err(g["X"], o.X)
+
+
 # ------------------------------------------------------------------ edge cases
 
 def test_zero_and_duplicate_rows():
