@@ -1436,13 +1436,19 @@ __device__ bool scan_team(const Team& T, const StreamDev& S, const CallArgs& A, 
           const double* rj = Rb + (size_t)jj * ldr;
           double v[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) v[i] = 0.0;
-          for (int c = lane; c < m; c += 32) {
-            const double x = rj[c];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const int t = warp + NWARP * i;
-              if (t >= jj && t < nrow) v[i] = fma(x, Rb[(size_t)t * ldr + c], v[i]);
+          for (int i = 0; i < 4; ++i) {
+            v[i] = 0.0;
+            const int t = warp + NWARP * i;
+            if (t >= jj && t < nrow) {  // the warp's live rows only (the test is warp-uniform)
+              const double* rt = Rb + (size_t)t * ldr;
+              double a0 = 0.0, a1 = 0.0;
+              int c = lane;
+              for (; c + 32 < m; c += 64) {
+                a0 = fma(rj[c], rt[c], a0);
+                a1 = fma(rj[c + 32], rt[c + 32], a1);
+              }
+              if (c < m) a0 = fma(rj[c], rt[c], a0);
+              v[i] = a0 + a1;
             }
           }
           warp_transpose_sum<double, 4>(v);
@@ -1586,27 +1592,50 @@ __device__ void section_apply_pu(const Team& T, const StreamDev& S, int q0, int 
   // per-row data of the section, staged once per CTA: flag, rank the row saw, append index,
   // 1/alpha of an appended row (one FP64 division per row, not per entry) and D
   __shared__ int fl_s[SLOW_MAX], rj_s[SLOW_MAX], q_s[SLOW_MAX];
-  __shared__ double ia_s[SLOW_MAX], d_s[SLOW_MAX];
+  __shared__ double ia_s[SLOW_MAX], d_s[SLOW_MAX], al_s[SLOW_MAX];
   __syncthreads();
   if (threadIdx.x < napp) {
     fl_s[threadIdx.x] = __ldcg(S.rowflag + q0 + threadIdx.x);
     d_s[threadIdx.x] = __ldcg(S.Dall + q0 + threadIdx.x);
+    if (VAR == VAR_ORTHONORMAL) al_s[threadIdx.x] = __ldcg(S.alpha + threadIdx.x);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {  // the rank each row saw and its append index (integers only)
     int rj = r, q = 0;
     for (int jj = 0; jj < napp; ++jj) {
       rj_s[jj] = rj;
       q_s[jj] = q;
-      ia_s[jj] = 1.0;
       if (fl_s[jj] != 1) {
-        if (VAR == VAR_ORTHONORMAL) ia_s[jj] = 1.0 / __ldcg(S.alpha + q);
         ++rj;
         ++q;
       }
     }
   }
   __syncthreads();
+  if (threadIdx.x < napp)  // one division per appended row, all rows at once
+    ia_s[threadIdx.x] = (VAR == VAR_ORTHONORMAL && fl_s[threadIdx.x] != 1) ? 1.0 / al_s[q_s[threadIdx.x]] : 1.0;
+  __syncthreads();
+  // the section rows' coordinate vectors g_j (gamma_j up to the rank the row saw; an
+  // appended row of the variants of Section 2.2 adds 1/alpha_j after them; zero beyond),
+  // staged once in the shared pool when they fit; the sums below run in the same order
+  // either way
+  const bool staged = (long long)napp * rnew <= POOL_DOUBLES;
+  double* gs = smem_pool();
+  if (staged) {
+    for (int e = threadIdx.x; e < napp * rnew; e += NT) {
+      const int jj = e / rnew, i = e - jj * rnew;
+      const int rj = rj_s[jj];
+      double v = 0.0;
+      if (fl_s[jj] == 1) {
+        if (i < rj) v = __ldcg(S.G + (size_t)(q0 + jj) * rm + i);
+      } else if (VAR != VAR_GENERAL) {
+        if (i < rj) v = __ldcg(S.Gind + (size_t)q_s[jj] * rm + i);
+        else if (i == rj) v = ia_s[jj];
+      }
+      gs[e] = v;
+    }
+    __syncthreads();
+  }
   const long long tstride = (long long)T.size() * NT;
   const long long nP = (long long)rnew * rnew;
   for (long long e = rr_thread(T); e < nP + rnew; e += tstride) {
@@ -1614,6 +1643,13 @@ __device__ void section_apply_pu(const Team& T, const StreamDev& S, int q0, int 
     const int i = isP ? (int)(e / rnew) : (int)(e - nP);
     const int l = isP ? (int)(e - (long long)i * rnew) : 0;
     double acc = 0.0;
+    if (staged) {
+      for (int jj = 0; jj < napp; ++jj) {
+        const double gi = gs[jj * rnew + i];
+        acc = fma(gi, isP ? gs[jj * rnew + l] : d_s[jj], acc);
+        if (VAR == VAR_GENERAL && fl_s[jj] != 1 && isP && i == rj_s[jj] && l == rj_s[jj]) acc += 1.0;
+      }
+    } else
     for (int jj = 0; jj < napp; ++jj) {
       const int rj = rj_s[jj];
       const double* g = S.G + (size_t)(q0 + jj) * rm;
@@ -1738,7 +1774,10 @@ __device__ int block_tail(const Team& T, const StreamDev& S, const CallArgs& A, 
     else
       phase_gamma<Team, false>(T, S, gam, q0, bend, r, ORTHO ? S.C : S.Ct);
     if (!T.sync()) return -1;
-    phase_reject<Team, false, 1>(T, S, gam, q0, bend, r, S.C, S.R);
+    // one-CTA teams: the section's rows as one 32-row item per column chunk (its items run
+    // one after another there, so fewer, larger items)
+    if constexpr (std::is_same<Team, CtaTeam>::value) phase_reject<Team, false, 8>(T, S, gam, q0, bend, r, S.C, S.R);
+    else phase_reject<Team, false, 1>(T, S, gam, q0, bend, r, S.C, S.R);
     if (!T.sync()) return -1;
     if (!scan_team<Team, VAR>(T, S, A, j0, q0, bend, r)) return -1;
     // the scan may have used the dynamic shared memory that caches the tensor-core B tiles
