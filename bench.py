@@ -41,8 +41,8 @@ WORKLOAD = f"single FP64 stream n={N_ROWS} m={M} r={R}, k={K_CALL} rows per rg_a
 # DRAM bytes (read + write) of one 32-row stream_kernel<false, false> launch, from the ncu
 # capture of that kernel summarised under profiles/, and the hash of the kernel sources it
 # was taken on: once the sources change the figure no longer applies (null).
-TRAFFIC_BYTES_PER_LAUNCH = 1480704
-TRAFFIC_SOURCES_SHA = "214473a8225c00e9"
+TRAFFIC_BYTES_PER_LAUNCH = 1481216
+TRAFFIC_SOURCES_SHA = "b2e6d45036b42f72"
 
 
 STREAM_KERNEL_SOURCES = ("rg_stream.cu", "rg_core.cuh", "rg_internal.cuh", "rg_tc.cuh")
@@ -869,7 +869,8 @@ def run_reference(args):
 def profile_case(name):
     """One untimed run of a small case of the hot path, for profilers (ncu -k/-c):
     stream-k32 / stream-kall (FP64 stream n=4096, m=1024, r=64 in 32-row calls / one
-    call), stream-kall-mixed, batch-uniform-{mixed,fp64} (152 instances of n=2048, m=256,
+    call), stream-kall-mixed, stream-tc-mixed (mixed, n=16384 in one call: its 8192-row
+    block takes the whole-GPU tensor-core path), batch-uniform-{mixed,fp64} (152 instances of n=2048, m=256,
     r=32), batch-uneven-mixed (the first 512 shapes of the 4096-instance batch), pinv
     (rg_pinv of an FP64 stream n=16384, m=1024, r=64 after one call)."""
     import torch
@@ -891,7 +892,10 @@ def profile_case(name):
     if name.startswith("stream"):
         mode = rg.RG_MIXED if name.endswith("mixed") else rg.RG_FP64
         k = 32 if name == "stream-k32" else 4096
-        s = inputs.large_stream(4096, M, R)
+        n = 4096
+        if name == "stream-tc-mixed":  # one call of 16384 rows: an 8192-row tensor-core block
+            k = n = 16384
+        s = inputs.large_stream(n, M, R)
         A = torch.from_numpy(s.A).to(dev)
         Y = torch.from_numpy(s.Y).to(dev)
         st = rg.RankGreville(M, 1e-10, mode)
@@ -932,7 +936,7 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--headline-only", action="store_true")
     ap.add_argument("--profile-case", default=None,
-                    choices=["stream-k32", "stream-kall", "stream-kall-mixed", "batch-uniform-mixed",
+                    choices=["stream-k32", "stream-kall", "stream-kall-mixed", "stream-tc-mixed", "batch-uniform-mixed",
                              "batch-uniform-fp64", "batch-uneven-mixed", "pinv"],
                     help="run one small untimed case for a profiler and exit")
     args = ap.parse_args()
