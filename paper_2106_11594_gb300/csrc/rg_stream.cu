@@ -1,39 +1,40 @@
 // rg_stream.cu -- rank-Greville update of ONE stream on the whole GPU.
 //
 // One rg_add_rows call is one cooperative persistent launch (one CTA per SM) that walks
-// the call's rows in internal blocks (rg_core.cuh). Per block of b rows:
+// the call's rows in internal blocks (process_rows in rg_core.cuh). Per block of b rows:
 //
-//  1. gamma  : gamma_j = Ct Gamma_j for all rows of the block against the block-start
-//              basis (Eq. label_eq_gnplusoneproj). Warp tiles, warp-shuffle reductions.
-//  2. reject : Gamma_r = Gamma_j - C^T gamma_j, with s_j = ||Gamma_r||^2 and
-//              t_j = ||Gamma_j||^2 accumulated in FP64 (Section 2.1, Eq.
-//              label_eq_schur_complement).
+//  1. gamma  : gamma_j = Ct Gamma_j (Q Gamma_j in the variants of Section 2.2) for all rows
+//              of the block against the block-start basis (Eq. label_eq_gnplusoneproj).
+//              Blocks of up to 64 rows: CTA tiles of up to 4 rows x BT basis rows whose
+//              columns are split evenly over the SM's four sub-partitions.
+//  2. reject : Gamma_r = Gamma_j - C^T gamma_j with the partial norms of s_j = ||Gamma_r||^2
+//              and t_j = ||Gamma_j||^2 per 64-column chunk, in FP64 (Section 2.1, Eq.
+//              label_eq_schur_complement). For small blocks, each item's basis tile arrives
+//              by bulk copy (TMA) during step 1, and the CTA that completes a row group sums
+//              its partials and takes the group's rank decisions.
 //  3. decide : rank test of Eq. label_eq_eps on every row. Dependent rows leave C and Ct
 //              unchanged (Theorem 6, dependent case), so every row before the first
 //              independent row is decided correctly against the block-start basis.
-//  4. update : the leading run of dependent rows is applied to P^-1 and w in steps of up
-//              to SB rows with the blocked form of the Sherman-Morrison update of
-//              Eq. label_eq_Pnplusoneinv_lindep_update (the Woodbury identity):
-//              Z = P^-1 G, M = I + G^T Z, P^-1 <- P^-1 - Z M^-1 Z^T, w <- w + Z M^-1 (y - G^T w),
-//              which equals SB successive single-row updates in exact arithmetic.
+//  4. update : the dependent run before the first special row goes into the information
+//              form P += sum gamma gamma^T, u += sum gamma (y - gamma^T w_b) (rg_core.cuh);
+//              a call of one small block defers it to the next launch, which folds it in
+//              on the CTAs the rejection leaves idle.
 //  5. rank changes: from the first independent (or, in mixed mode, candidate) row on, up
-//              to SLOW_MAX rows are re-projected in FP64 and scanned in order by one CTA:
-//              rank test, append (Theorem 6, independent case) and an in-block fix-up of
-//              the later rows of the section (their rejections lose the new direction:
-//              Gamma_r,t -= kappa Gamma_r,j with kappa = K_j^T Gamma_r,t). The dependent
-//              runs between appends go through step 4; the appends to C and Ct are applied
-//              as one low-rank product afterwards.
+//              to SLOW_MAX rows are re-projected in FP64 and scanned in order: rank test,
+//              append (Theorem 6, independent case) and a fix-up of the later rows of the
+//              section (their rejections lose the new direction: Gamma_r,t -= kappa
+//              Gamma_r,j), then the section's P/u update and one low-rank update of C and Ct.
 //
-// The solution is kept in coordinates w (X = Ct^T w, which follows from
-// A^+ = Ct^T P^-1 B^T, Section 2.1): the a-priori error is y - Gamma^T X = y - gamma^T w,
-// a dependent row adds zeta (y - gamma^T w) / (1 + gamma^T zeta) to w (Theorem 5) and an
-// independent row appends y to w (Theorem 4). X is materialised on request.
+// The solution is kept in coordinates w = w_b + P^-1 u (X = Ct^T w, from
+// A^+ = Ct^T P^-1 B^T, Section 2.1); P^-1 and w are formed (Cholesky of P) only when X or
+// an export is requested.
 //
 // FP64 mode keeps the general factorization of Algorithm 1 (C = selected rows, Ct its dual
-// basis). Mixed mode keeps the orthonormal variant of Section 2.2 (alpha = 1/||Gamma_r||:
-// Ct = C = Q), projects in FP32 against an FP32 copy of Q, and re-decides every row whose
-// FP32 relative rejection exceeds the floor tau_lo in FP64. FP64 mode can also keep either
-// variant of Section 2.2 (RG_ORTHONORMAL, RG_ORTHOGONAL).
+// basis), or either variant of Section 2.2 (RG_ORTHONORMAL, RG_ORTHOGONAL). Mixed mode keeps
+// the orthonormal variant (alpha = 1/||Gamma_r||: Ct = C = Q), projects in FP32 against an
+// FP32 copy of Q, and re-decides in FP64 every row whose FP32 relative rejection exceeds the
+// floor tau_lo. Its calls of at least TC_GRID_MIN rows run in stream_tc_kernel, where blocks
+// of that size project 128-row chunks per CTA on the tensor cores (3xTF32, rg_tc.cuh).
 #include <cuda_runtime.h>
 
 #include <algorithm>
