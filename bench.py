@@ -695,7 +695,8 @@ def run_batched(bat, mode, steps, warmup, dev, ws=1, rank=0, backward=False, sm_
             gX.mul_(2.0)
             bt.adjoint(A, ro, eo, Y, Y.numel(), gX, gA, gY)
 
-    kb, kb_times = autotune.tune_block_rows(bt, A, ro, eo, Y, X)
+    choice, tune_times = autotune.tune(bt, A, ro, eo, Y, X,
+                                       tc_groups=(2, 4, 6) if (mode & rg.RG_MIXED) else None)
     graph = None
     cap_stream = torch.cuda.Stream()
     cap_stream.wait_stream(torch.cuda.current_stream())
@@ -740,8 +741,8 @@ def run_batched(bat, mode, steps, warmup, dev, ws=1, rank=0, backward=False, sm_
     kind = "fp64" if not (mode & rg.RG_MIXED) else "mixed_tc"
     out = {"rows_per_s": rate, "ms_per_step": ms, "rows": int(rows),
            "instances": len(bat.all_shapes), "rank_match_generator": int(match),
-           "cuda_graph": graph is not None, "block_rows": kb,
-           "autotune_ms": {str(k): round(v, 3) for k, v in kb_times.items()},
+           "cuda_graph": graph is not None, "autotuned": choice,
+           "autotune_ms": {k: round(v, 3) for k, v in tune_times.items()},
            "roofline": roofline_entry(bat.n, bat.m, np.minimum(bat.n, bat.r), ms / 1e3, kind, sm_mhz)}
     if backward:
         out["roofline"]["note"] = "forward cost only; the step also holds the adjoint"

@@ -310,6 +310,18 @@ rg_status rg_batch_set_stream(rg_batch* bt, void* cuda_stream);
  */
 rg_status rg_batch_set_block_rows(rg_batch* bt, int64_t rows, int64_t* rows_out);
 
+/*
+ * rg_batch_set_tc_group -- mixed mode's tensor-core block projection (the products of
+ * Section 3's block of observations against the block-start basis, 3xTF32): how many
+ * 64-column slices of the second product (the rejections Gamma - G Q) are issued back to
+ * back into their own tensor-memory accumulators before one wait. group > 0 sets it
+ * (1 <= group <= 6, otherwise RG_EINVAL); group <= 0 only queries. group_out (host, may be
+ * NULL) receives the value in force (default 6). Host-side only; takes effect at the next
+ * rg_batch_add_rows; no effect in FP64 mode. Results do not depend on it. Used by the
+ * autotuner.
+ */
+rg_status rg_batch_set_tc_group(rg_batch* bt, int64_t group, int64_t* group_out);
+
 /* rg_batch_sync -- wait and return any pending device error of the batch. */
 rg_status rg_batch_sync(rg_batch* bt);
 

@@ -25,6 +25,7 @@ namespace rg {
 struct BatchDev {
   int B, mixed, ortho, orthog, test_mode, kb_max, ld_max, r_max_max, nmc_max;
   int kb_cap;  // rows of block scratch laid out per CTA (kb_max <= kb_cap)
+  int tc_group;  // mixed mode: second-product column slices issued per commit (1..TC_NG2)
   double tol, tau_lo;
   const int* m;               // B
   const int* r_max;           // B
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) batch_kernel(BatchDev D, co
   extern __shared__ __align__(1024) unsigned char dyn_smem[];
   float* const dyn_base = reinterpret_cast<float*>(
       (reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~static_cast<uintptr_t>(1023));
-  if (MIXED) tc_ctx_init(&tcx, &tc_bar, &tc_tmem, dyn_base, TC_SMEM_MIXED);
+  if (MIXED) tc_ctx_init(&tcx, &tc_bar, &tc_tmem, dyn_base, TC_SMEM_MIXED, D.tc_group);
   StreamDev S{};
   S.tcx = MIXED ? (void*)&tcx : nullptr;
   S.Rs = reinterpret_cast<double*>(dyn_base);
@@ -430,6 +431,7 @@ rg_status rg_batch_init(rg_batch** out, int64_t B, const int64_t* m, double tol,
   while (kb > 32 && (size_t)kb * rmm * 8 > (size_t)4 << 20) kb /= 2;
   D.kb_cap = kb;
   D.kb_max = std::min(kb, 256);
+  D.tc_group = TC_NG2;
   int nsm = 0, per = 0;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, bt->device);
   const int dyn = D.mixed ? TC_SMEM_MIXED : TC_SMEM;
@@ -617,6 +619,17 @@ rg_status rg_batch_set_block_rows(rg_batch* bt, int64_t rows, int64_t* rows_out)
     bt->D.kb_max = (int)rows;
   }
   if (rows_out) *rows_out = bt->D.kb_max;
+  return RG_OK;
+}
+
+rg_status rg_batch_set_tc_group(rg_batch* bt, int64_t group, int64_t* group_out) {
+  if (!valid_batch(bt)) return fail(RG_EINVAL, "rg_batch_set_tc_group: invalid batch");
+  if (group > 0) {
+    if (group > TC_NG2)
+      return fail(RG_EINVAL, "rg_batch_set_tc_group: %lld outside [1, %d]", (long long)group, TC_NG2);
+    bt->D.tc_group = (int)group;
+  }
+  if (group_out) *group_out = bt->D.tc_group;
   return RG_OK;
 }
 

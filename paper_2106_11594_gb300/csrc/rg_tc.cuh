@@ -53,6 +53,7 @@ struct TcCtx {
   int cache_cap;            // floats available for the B-tile cache at Bhi (0: none)
   const float* cq;          // basis whose tiles are cached (with rank cr), or null
   int cr;
+  int ng2;                  // second-product column slices issued per commit (1..TC_NG2)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -272,7 +273,7 @@ __device__ __forceinline__ uint32_t dyn_smem_bytes() {
 // tiles Ahi, Alo, Bhi, Blo, the rest after Bhi being the B-tile cache. Every thread calls
 // it; tc_ctx_release frees the tensor memory before the CTA exits.
 __device__ __forceinline__ void tc_ctx_init(TcCtx* tcx, unsigned long long* bar, uint32_t* tmem_slot,
-                                            float* dyn_base, int smem_bytes) {
+                                            float* dyn_base, int smem_bytes, int ng2 = TC_NG2) {
   if (threadIdx.x < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(TC_TMEM_COLS));
@@ -290,6 +291,7 @@ __device__ __forceinline__ void tc_ctx_init(TcCtx* tcx, unsigned long long* bar,
     tcx->cache_cap = (smem_bytes - 1024) / 4 - 2 * TC_TILE;
     tcx->cq = nullptr;
     tcx->cr = -1;
+    tcx->ng2 = min(max(ng2, 1), TC_NG2);
   }
   tc_fence_before();
   __syncthreads();
@@ -542,7 +544,7 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
       }
     };
     if (cached && nk2 == 1) {
-      // A = G staged once; up to TC_NG2 column slices issued back to back into their own
+      // A = G staged once; up to X.ng2 column slices issued back to back into their own
       // accumulators (independent MMA chains), one commit and one wait per group
       if (half == 0) {
         float g[32];
@@ -556,8 +558,8 @@ static __device__ int tc_project_block(TcCtx* Xp, const StreamDev& S, const doub
           X.Alo[o] = l;
         }
       }
-      for (int g0 = 0; g0 < nns; g0 += TC_NG2) {
-        const int ng = min(TC_NG2, nns - g0);
+      for (int g0 = 0; g0 < nns; g0 += X.ng2) {
+        const int ng = min(X.ng2, nns - g0);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();

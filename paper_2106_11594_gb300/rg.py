@@ -74,6 +74,7 @@ def lib(build: bool = True):
         "rg_set_screen": [vp, f64],
         "rg_batch_set_screen": [vp, f64],
         "rg_batch_set_block_rows": [vp, i64, vp],
+        "rg_batch_set_tc_group": [vp, i64, vp],
         "rg_snapshot_size": [vp, vp],
         "rg_snapshot": [vp, vp, i64],
         "rg_restore": [vp, vp, i64],
@@ -311,6 +312,14 @@ class RankGrevilleBatch:
         out = ctypes.c_int64(0)
         _check(lib().rg_batch_set_block_rows(self._h, int(rows), ctypes.byref(out)),
                "rg_batch_set_block_rows")
+        return int(out.value)
+
+    def tc_group(self, group: int = 0) -> int:
+        """Set (group > 0) and/or return the second-product slices per tensor-core commit
+        (rg_batch_set_tc_group)."""
+        out = ctypes.c_int64(0)
+        _check(lib().rg_batch_set_tc_group(self._h, int(group), ctypes.byref(out)),
+               "rg_batch_set_tc_group")
         return int(out.value)
 
     def sync(self):

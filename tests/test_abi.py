@@ -67,3 +67,12 @@ def test_flag_validation_without_gpu():
     for flags in (rg.RG_ORTHOGONAL | rg.RG_MIXED, rg.RG_ORTHOGONAL | rg.RG_ORTHONORMAL, 64):
         assert L.rg_init(ct.byref(h), 16, 1e-10, flags, 0, None) == rg.RG_EINVAL
         assert not h.value
+
+
+def test_batch_knobs_reject_a_null_handle_without_gpu():
+    import ctypes as ct
+    L = rg.lib()
+    out = ct.c_int64(-1)
+    assert L.rg_batch_set_tc_group(None, 4, ct.byref(out)) == rg.RG_EINVAL
+    assert L.rg_batch_set_block_rows(None, 64, ct.byref(out)) == rg.RG_EINVAL
+    assert out.value == -1

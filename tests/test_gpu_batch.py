@@ -178,3 +178,44 @@ def test_block_rows_cap():
             assert int(ranks[b]) == o.rank
             assert checks.rel_err(X.cpu().numpy()[xo[b]:xo[b + 1]], o.X) <= 1e-10
     bt.close()
+
+
+def test_tc_group_and_autotuner_mixed():
+    """The tensor-core slice grouping changes only how the second product's MMAs are
+    batched: every value gives bit-identical results (and the oracle's ranks and X within
+    1e-4); out-of-range values are refused; the autotuner leaves a candidate pair set."""
+    torch, dev = torch_cuda()
+    from paper_2106_11594_gb300 import autotune
+    batch = inputs.uniform_batch(1024, instances=range(6))
+    ores = oracle_batch(batch)
+    m = np.array([s.m for s in batch.streams], dtype=np.int64)
+    bt = rg.RankGrevilleBatch(m, 1e-10, rg.RG_MIXED)
+    assert bt.tc_group() == 6
+    for bad in (7, 100):
+        with pytest.raises(rg.RGError):
+            bt.tc_group(bad)
+    A, Y, ro, eo = (torch.from_numpy(a).to(dev) for a in batch.packed()[:4])
+    xo = np.concatenate([[0], np.cumsum(m)])
+    ref = None
+    for g in (1, 3, 6):
+        assert bt.tc_group(g) == g
+        X = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+        ranks = torch.empty(len(m), dtype=torch.int64, device=dev)
+        bt.reset()
+        bt.add_rows(A, ro, eo, Y)
+        bt.solution(X, None, ranks)
+        bt.sync()
+        Xh = X.cpu().numpy()
+        if ref is None:
+            ref = Xh
+            for b, o in enumerate(ores):
+                assert int(ranks[b]) == o.rank
+                assert checks.rel_err(Xh[xo[b]:xo[b + 1]], o.X) <= 1e-4
+        else:
+            np.testing.assert_array_equal(Xh, ref)
+    X = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+    choice, times = autotune.tune(bt, A, ro, eo, Y, X, block_rows=(128, 256), tc_groups=(2, 6))
+    assert choice["block_rows"] in (128, 256) and choice["tc_group"] in (2, 6)
+    assert set(times) == {"128/2", "128/6", "256/2", "256/6"}
+    assert bt.block_rows() == choice["block_rows"] and bt.tc_group() == choice["tc_group"]
+    bt.close()
