@@ -42,7 +42,7 @@ WORKLOAD = f"single FP64 stream n={N_ROWS} m={M} r={R}, k={K_CALL} rows per rg_a
 # capture of that kernel summarised under profiles/, and the hash of the kernel sources it
 # was taken on: once the sources change the figure no longer applies (null).
 TRAFFIC_BYTES_PER_LAUNCH = 1481216
-TRAFFIC_SOURCES_SHA = "ac5fe192730dbfea"
+TRAFFIC_SOURCES_SHA = "7f40ea73177d5281"
 
 
 STREAM_KERNEL_SOURCES = ("rg_stream.cu", "rg_core.cuh", "rg_internal.cuh", "rg_tc.cuh")

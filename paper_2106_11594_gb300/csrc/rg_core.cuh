@@ -1748,6 +1748,14 @@ __device__ void section_apply_basis(const Team& T, const StreamDev& S, const Cal
 //  * otherwise: worker 0 decides; the dependent run before the first special row is
 //    accumulated; from that row the sequential FP64 section applies the rank changes.
 // =======================================================================================
+// Growth factor of the block size after a block whose rows were all dependent (it falls
+// back to KB_MIN after a rank change): 2, except for mixed mode on the whole GPU, where
+// blocks of TC_GRID_MIN rows and more go to the tensor cores and are reached sooner with 4.
+template <class Team, bool F32>
+__device__ __forceinline__ int kb_growth() {
+  return (F32 && std::is_same<Team, GridTeam>::value) ? 4 : 2;
+}
+
 // Steps 4 and 5 of a block whose rows [0, b) (call rows j0 + [0, b)) have their gamma in
 // S.G, their norms in S.s / S.t and their a-priori errors in S.Dall, and whose first row
 // that needs the sequential section is q0 (b if none): the dependent run before q0 (unless
@@ -1803,7 +1811,7 @@ __device__ int block_tail(const Team& T, const StreamDev& S, const CallArgs& A, 
     if (threadIdx.x == 0) {
       *S.rows_seen = __ldcg(S.rows_seen) + applied;
       S.ctrl[CTRL_R] = rnew;
-      S.ctrl[CTRL_KB] = (q0 < b) ? min(KB_MIN, S.kb_max) : min(2 * kb0, S.kb_max);
+      S.ctrl[CTRL_KB] = (q0 < b) ? min(KB_MIN, S.kb_max) : min(kb_growth<Team, F32>() * kb0, S.kb_max);
       S.ctrl[CTRL_PEND] = 1;
       S.ctrl[CTRL_PEND_ROWS] = 0;
     }
@@ -1988,7 +1996,7 @@ __device__ bool process_rows(const Team& T, const StreamDev& S, const CallArgs& 
               for (int j = threadIdx.x; j < b; j += NT) A.indep[j0 + j] = 0;
             if (threadIdx.x == 0) {
               *S.rows_seen = __ldcg(S.rows_seen) + b;
-              S.ctrl[CTRL_KB] = min(2 * kb0, S.kb_max);
+              S.ctrl[CTRL_KB] = min(kb_growth<Team, F32>() * kb0, S.kb_max);
               S.ctrl[CTRL_PEND] = 1;
               S.ctrl[CTRL_PEND_ROWS] = defer ? b : 0;
             }
