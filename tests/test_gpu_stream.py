@@ -106,23 +106,26 @@ def _late_growth_stream(n, m, rank, late, seed):
     return A, Y
 
 
-@pytest.mark.parametrize("case", ["ragged", "late_growth", "rank_80"])
+@pytest.mark.parametrize("case", ["ragged", "late_growth", "rank_80", "odd_m"])
 def test_mixed_large_calls_tensor_core_blocks(case):
     """One mixed-mode call of >= 8192 rows runs its blocks of >= 8192 rows through the
-    tensor-core chunk path on the whole GPU. The blocks double from 64 rows after the last
-    rank change, so with m = 512:
-      ragged      - rank 40; blocks of 8192 rows at row 8192 and of 8200 rows at 16384
-                    (65 chunks, the last of 8 rows);
-      late_growth - as ragged, plus two new directions at rows 20000 and 20001, inside the
-                    8200-row block: the chunks' fused sums are discarded, the 3616 rows before
-                    the first are summed again from G, and the FP64 section takes both;
-      rank_80     - rank 80 (above the shared-memory staging of the fused sums): the
-                    8192-row block at row 8224 sums its rows from G.
+    tensor-core chunk path on the whole GPU. After the rank-growth sections the blocks grow
+    x4 from 64 rows (64, 256, 1024, 4096), so the block after them holds the rest of the
+    call:
+      ragged      - m = 512, rank 40: an 8200-row block at row 5504 (64 chunks and one of
+                    8 rows);
+      late_growth - as ragged, plus two new directions at rows 10000 and 10001, inside that
+                    block: the chunks' fused sums are discarded, the 4496 rows before the
+                    first are summed again from G, and the FP64 section takes both;
+      rank_80     - m = 512, rank 80 (above the shared-memory staging of the fused sums):
+                    an 8250-row block at row 5536 sums its rows from G;
+      odd_m       - m = 333 (row starts off 16-byte boundaries), rank 40: an 8300-row block.
     Flags and basis rows as integer arrays and X within 1e-4 of the FP64 oracle."""
-    n, m = {"ragged": (24584, 512), "late_growth": (24584, 512), "rank_80": (16416, 512)}[case]
-    rank = 80 if case == "rank_80" else 40
-    late = [20000, 20001] if case == "late_growth" else []
-    A, Y = _late_growth_stream(n, m, rank, late, seed={"ragged": 11, "late_growth": 12, "rank_80": 13}[case])
+    n, m, rank = {"ragged": (13704, 512, 40), "late_growth": (13704, 512, 40),
+                  "rank_80": (13786, 512, 80), "odd_m": (13804, 333, 40)}[case]
+    late = [10000, 10001] if case == "late_growth" else []
+    seed = {"ragged": 11, "late_growth": 12, "rank_80": 13, "odd_m": 14}[case]
+    A, Y = _late_growth_stream(n, m, rank, late, seed=seed)
     o = fp64.solve(A, Y, tol=1e-10)
     assert o.rank == rank + len(late)
     g = run_stream(A, Y, n, mode=rg.RG_MIXED, export=True)
